@@ -1,0 +1,184 @@
+/*
+ * tidas.h -- C ABI of the GB300 (sm_103a) Delay-and-Sum / tiDAS library.
+ *
+ * Method: C. Razzetta et al., "tiDAS: a time invariant approximation of the
+ * Delay and Sum algorithm for biomedical ultrasound PSF reconstructions",
+ * arXiv 2507.15464.  Each entry point cites the section / equation that
+ * defines the operation it computes.
+ *
+ * Conventions shared by every call
+ *  - Array arguments are DEVICE pointers owned by the caller, C-contiguous,
+ *    with the layout given beside each argument.  The library never frees
+ *    them and never keeps them after the call returns.  A plan owns only its
+ *    own tables, freed by das_plan_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return without synchronising;
+ *    outputs are overwritten, never accumulated into.
+ *  - Every call returns TIDAS_OK (0) or a negative status; the text of the
+ *    last error of the calling thread is returned by tidas_last_error().
+ *    Argument errors are detected before anything is enqueued.  Kernels
+ *    that wait on asynchronous copies or tensor-core completions use bounded
+ *    waits: if one gives up, the kernel records it in a device flag and
+ *    returns; tidas_device_status() reads and clears that flag.
+ *  - Geometry: linear array on z = 0, element centres
+ *    x_n = (n - (n_elem-1)/2) * pitch (Section 2.1); pixel (ix, iz) at
+ *    x = x0 + (ix + 1/2) dx, z = z0 + (iz + 1/2) dz; time of sample k is
+ *    t0 + k / fs.  Transmit events are plane waves at angles_rad[a].
+ *  - Channel data rf: [n_frames][n_angles][n_elem][n_samples], float32 or
+ *    IEEE half (params.rf_dtype).  Images and reflectivity maps:
+ *    [n_frames][nz][nx] float32 (x contiguous).
+ */
+#ifndef TIDAS_H
+#define TIDAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TIDAS_OK 0
+#define TIDAS_ERR_ARG (-1)         /* bad argument: null pointer, size, alignment, dtype */
+#define TIDAS_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define TIDAS_ERR_TIMEOUT (-3)     /* a bounded device wait gave up (see tidas_device_status) */
+#define TIDAS_ERR_UNSUPPORTED (-4) /* valid request this build does not implement */
+
+#define TIDAS_RF_F32 0
+#define TIDAS_RF_F16 1
+
+#define TIDAS_INTERP_LINEAR 0
+#define TIDAS_INTERP_CUBIC 1 /* Keys kernel, a = -0.5, samples floor(u)-1 .. floor(u)+2 */
+
+#define TIDAS_VARIANT_DIRECT 0    /* FP32 direct convolution on CUDA cores */
+#define TIDAS_VARIANT_GEMM_BF16 1 /* Toeplitz GEMM on tcgen05 tensor cores, BF16 in, FP32 acc */
+#define TIDAS_VARIANT_GEMM_RESID 2 /* BF16 GEMM + low-part residual products, FP32 in/out */
+
+/* Acquisition and reconstruction parameters (SI units). */
+typedef struct {
+    int32_t n_elem;            /* array elements */
+    double pitch;              /* element spacing, m */
+    double f0;                 /* pulse centre frequency, Hz */
+    double fs;                 /* sampling rate, Hz */
+    double c;                  /* speed of sound, m/s (Eq. (2.3)) */
+    double frac_bw;            /* -6 dB fractional bandwidth of the Gaussian pulse */
+    int32_t n_angles;          /* plane-wave transmit events */
+    const double* angles_rad;  /* HOST array [n_angles]; copied by das_plan_create */
+    int32_t n_samples;         /* samples per channel */
+    double t0;                 /* time of sample 0, s */
+    int32_t nx, nz;            /* image grid: lateral, axial pixel counts */
+    double x0, dx, z0, dz;     /* grid origin and spacing, m */
+    int32_t interp;            /* TIDAS_INTERP_* */
+    double fnum;               /* receive f-number; <= 0: whole array, unit weights */
+    int32_t rf_dtype;          /* TIDAS_RF_F32 or TIDAS_RF_F16 (channel-data storage) */
+} das_params;
+
+typedef struct das_plan_s* das_plan;
+
+/* Validate `params`, copy them, and build the plan's device tables: per
+ * (angle, column) and (angle, row) splits of the plane-wave transmit delay
+ * into an integer sample and an FP32 fraction (built in FP64), per
+ * (element, column) lateral offsets in samples, per-row depths.  Sizes:
+ * 1 <= n_elem <= 1024, 1 <= n_angles <= 16, 4 <= n_samples <= 2^22,
+ * 1 <= nx, nz <= 8192, dx, dz, pitch, c, fs, f0 > 0, 0 < frac_bw <= 2.
+ * Synchronous (allocates and uploads).  *out_plan receives the handle. */
+int das_plan_create(const das_params* params, das_plan* out_plan);
+
+/* Free the plan's device tables.  Waits for the device first.  NULL is a no-op. */
+int das_plan_destroy(das_plan plan);
+
+/* Channel data of point scatterers under the Born approximation, Eq. (2.1):
+ * rf[f][a][n][k] = sum_j Re(A_fj * p(t_k - tau_a,n(x_fj, z_fj))), with the
+ * Gaussian-modulated pulse p (6 dB band f0(1 +- frac_bw/2), truncated at the
+ * -60 dB envelope) and round-trip time of flight
+ * tau = (x sin(theta_a) + z cos(theta_a) + sqrt((x - x_n)^2 + z^2)) / c.
+ *   pos_xz [n_frames][n_scat][2] float64 (x, z), metres
+ *   amp    [n_frames][n_scat][2] float32 (Re A, Im A)
+ *   rf     [n_frames][n_angles][n_elem][n_samples], plan's rf_dtype (output)
+ * Delays are evaluated in FP64 per (scatterer, angle, element); samples are
+ * accumulated in FP32 (summation order is not fixed). */
+int das_synthesize(das_plan plan, const double* pos_xz, const float* amp, int32_t n_scat,
+                   int32_t n_frames, void* rf, void* stream);
+
+/* Eq. (2.1) for real reflectivities sitting on the pixel centres (the
+ * forward operator A of deconvolution):
+ *   refl [n_frames][nz][nx] float32 -> rf [n_frames][n_angles][n_elem][n_samples]
+ * (rf_dtype must be TIDAS_RF_F32).  Exact transpose of das_synthesize_adjoint. */
+int das_synthesize_grid(das_plan plan, const float* refl, void* rf, int32_t n_frames,
+                        void* stream);
+
+/* Transpose of das_synthesize_grid (A^T): every pixel correlates the channel
+ * data with the pulse delayed to its own round-trip time:
+ *   rf [n_frames][n_angles][n_elem][n_samples] float32 -> refl [n_frames][nz][nx] float32 */
+int das_synthesize_adjoint(das_plan plan, const void* rf, float* refl, int32_t n_frames,
+                           void* stream);
+
+/* Delay and Sum, Eq. (2.2), compounded coherently over the angles:
+ * img[f][iz][ix] = sum_a sum_n w_n(x, z) * S_{f,a,n}(u), with
+ * u = (tau_tx + tau_rx - t0) fs samples, S sampled with the plan's
+ * interpolation (zero outside [0, n_samples)), and the Hann receive
+ * aperture w = cos^2(pi (x - x_n) F# / z) for |x - x_n| <= z / (2 F#)
+ * (Section 3.1 fixes the f-number).  Accumulation is FP32.
+ *   rf  [n_frames][n_angles][n_elem][n_samples], plan's rf_dtype
+ *   img [n_frames][nz][nx] float32 (output) */
+int das_forward(das_plan plan, const void* rf, float* img, int32_t n_frames, void* stream);
+
+/* Transpose of das_forward (B^T), for FP32 channel data plans:
+ *   img [n_frames][nz][nx] float32 -> rf [n_frames][n_angles][n_elem][n_samples] float32
+ * Each channel sample gathers w * (interpolation weight) * img from the
+ * pixels that read it; the result is deterministic. */
+int das_adjoint(das_plan plan, const float* img, float* rf, int32_t n_frames, void* stream);
+
+/* Delay-index table of one angle, the integer/fraction split of
+ * u = ((x sin(theta) + z cos(theta) + sqrt((x - x_n)^2 + z^2)) / c - t0) * fs
+ * evaluated in FP64 with every operation rounded separately (no fused
+ * multiply-add), in that order; Eq. (2.3) generalised to steered plane waves:
+ *   idx  [nz][nx][n_elem] int32  = floor(u)
+ *   frac [nz][nx][n_elem] float32 = u - floor(u), rounded to nearest. */
+int das_delay_table(das_plan plan, int32_t angle, int32_t* idx, float* frac, void* stream);
+
+/* tiDAS kernels from exact single-scatterer PSFs (Sections 2.2-2.3,
+ * Eq. (2.6)-(2.8)).  For every row iz a unit scatterer on pixel (ic, iz),
+ * ic = nx / 2, is synthesised and beamformed by the plan's DAS; the kernel
+ * of row iz is that PSF row at columns ic + t - taps/2, t = 0..taps-1.
+ * ref_stride > 1: rows share the PSF of a reference row s (the middle row
+ * of each block of ref_stride rows) scaled by the least-squares weight of
+ * Eq. (2.12), theta = <h_s, h_iz> / <h_s, h_s>.
+ *   kernels [nz][taps] float32 (output), theta [nz] float32 or NULL (output;
+ *   all ones when ref_stride <= 1).  1 <= taps <= 255. */
+int tidas_fit_kernels(das_plan plan, int32_t taps, int32_t ref_stride, float* kernels,
+                      float* theta, void* stream);
+
+/* tiDAS forward, the convolutional line model of Eq. (2.13) applied row by
+ * row along the lateral axis with depth-dependent kernels:
+ *   img[f][iz][ix] = sum_t h_iz[t] * refl[f][iz][ix - t + taps/2]   (zero outside)
+ *   kernels [nz][taps] float32
+ *   refl    [n_frames][nz][nx]: float32 (variants DIRECT, GEMM_RESID) or
+ *           bfloat16 (variant GEMM_BF16)
+ *   img     [n_frames][nz][nx] float32 (output)
+ * GEMM variants: each row is Y[frames x nx] = R[frames x nx] * T(h_iz) with
+ * T the banded Toeplitz matrix of the kernel, on tcgen05 tensor cores with
+ * FP32 accumulation in tensor memory; they need taps <= 63, nx % 8 == 0 and
+ * 16-byte aligned refl / img.  GEMM_RESID splits refl and kernels into BF16
+ * high and low parts and adds the two first-order low-part products. */
+int tidas_forward(const float* kernels, int32_t taps, int32_t nz, int32_t nx, const void* refl,
+                  float* img, int32_t n_frames, int32_t variant, void* stream);
+
+/* Transpose of tidas_forward (correlation with the same kernels):
+ *   refl[f][iz][j] = sum_t h_iz[t] * img[f][iz][j + t - taps/2]
+ * Argument types as tidas_forward with the roles of refl and img exchanged
+ * (img is the input: bfloat16 for GEMM_BF16, else float32; refl is float32). */
+int tidas_adjoint(const float* kernels, int32_t taps, int32_t nz, int32_t nx, const void* img,
+                  float* refl, int32_t n_frames, int32_t variant, void* stream);
+
+/* Text of the calling thread's last error ("" if none). */
+const char* tidas_last_error(void);
+
+/* Synchronise the device, then read and clear the bounded-wait flag of the
+ * tensor-core kernels: *status = 0 if no wait gave up since the last call,
+ * otherwise a code naming the wait.  Returns TIDAS_ERR_TIMEOUT when set. */
+int tidas_device_status(int32_t* status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TIDAS_H */

@@ -1,0 +1,143 @@
+"""ctypes binding of libtidas.so with the C ABI's names (argument marshalling only).
+
+Every function takes raw device pointers (ints) and a stream handle, exactly
+as declared in include/tidas.h, and raises TidasError on a non-zero status.
+There is no fallback: if the library cannot be loaded the import fails.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+TIDAS_OK, TIDAS_ERR_ARG, TIDAS_ERR_CUDA, TIDAS_ERR_TIMEOUT, TIDAS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4
+RF_F32, RF_F16 = 0, 1
+INTERP_LINEAR, INTERP_CUBIC = 0, 1
+VARIANT_DIRECT, VARIANT_GEMM_BF16, VARIANT_GEMM_RESID = 0, 1, 2
+
+
+class TidasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("tidas status %d: %s" % (code, msg))
+        self.code = code
+
+
+class das_params(ctypes.Structure):
+    _fields_ = [
+        ("n_elem", ctypes.c_int32), ("pitch", ctypes.c_double), ("f0", ctypes.c_double),
+        ("fs", ctypes.c_double), ("c", ctypes.c_double), ("frac_bw", ctypes.c_double),
+        ("n_angles", ctypes.c_int32), ("angles_rad", ctypes.POINTER(ctypes.c_double)),
+        ("n_samples", ctypes.c_int32), ("t0", ctypes.c_double),
+        ("nx", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("x0", ctypes.c_double), ("dx", ctypes.c_double),
+        ("z0", ctypes.c_double), ("dz", ctypes.c_double),
+        ("interp", ctypes.c_int32), ("fnum", ctypes.c_double), ("rf_dtype", ctypes.c_int32),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_SIG = {
+    "das_plan_create": [ctypes.POINTER(das_params), ctypes.POINTER(ctypes.c_void_p)],
+    "das_plan_destroy": [_P],
+    "das_synthesize": [_P, _P, _P, _I, _I, _P, _P],
+    "das_synthesize_grid": [_P, _P, _P, _I, _P],
+    "das_synthesize_adjoint": [_P, _P, _P, _I, _P],
+    "das_forward": [_P, _P, _P, _I, _P],
+    "das_adjoint": [_P, _P, _P, _I, _P],
+    "das_delay_table": [_P, _I, _P, _P, _P],
+    "tidas_fit_kernels": [_P, _I, _I, _P, _P, _P],
+    "tidas_forward": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
+    "tidas_adjoint": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
+    "tidas_device_status": [ctypes.POINTER(ctypes.c_int32)],
+}
+EXPORTED = list(_SIG) + ["tidas_last_error"]
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libtidas.so (building it first if absent).  Raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError("libtidas.so has not been built: run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, args in _SIG.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.tidas_last_error.argtypes = []
+    L.tidas_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != TIDAS_OK:
+        msg = load().tidas_last_error().decode(errors="replace")
+        raise TidasError(rc, msg)
+    return rc
+
+
+def das_plan_create(params: das_params):
+    h = ctypes.c_void_p()
+    _check(load().das_plan_create(ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def das_plan_destroy(plan):
+    return _check(load().das_plan_destroy(plan))
+
+
+def das_synthesize(plan, pos_xz, amp, n_scat, n_frames, rf, stream=0):
+    return _check(load().das_synthesize(plan, pos_xz, amp, n_scat, n_frames, rf, stream))
+
+
+def das_synthesize_grid(plan, refl, rf, n_frames, stream=0):
+    return _check(load().das_synthesize_grid(plan, refl, rf, n_frames, stream))
+
+
+def das_synthesize_adjoint(plan, rf, refl, n_frames, stream=0):
+    return _check(load().das_synthesize_adjoint(plan, rf, refl, n_frames, stream))
+
+
+def das_forward(plan, rf, img, n_frames, stream=0):
+    return _check(load().das_forward(plan, rf, img, n_frames, stream))
+
+
+def das_adjoint(plan, img, rf, n_frames, stream=0):
+    return _check(load().das_adjoint(plan, img, rf, n_frames, stream))
+
+
+def das_delay_table(plan, angle, idx, frac, stream=0):
+    return _check(load().das_delay_table(plan, angle, idx, frac, stream))
+
+
+def tidas_fit_kernels(plan, taps, ref_stride, kernels, theta, stream=0):
+    return _check(load().tidas_fit_kernels(plan, taps, ref_stride, kernels, theta, stream))
+
+
+def tidas_forward(kernels, taps, nz, nx, refl, img, n_frames, variant, stream=0):
+    return _check(load().tidas_forward(kernels, taps, nz, nx, refl, img, n_frames, variant, stream))
+
+
+def tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream=0):
+    return _check(load().tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream))
+
+
+def tidas_device_status():
+    v = ctypes.c_int32(0)
+    _check(load().tidas_device_status(ctypes.byref(v)))
+    return v.value
+
+
+def tidas_last_error():
+    return load().tidas_last_error().decode(errors="replace")

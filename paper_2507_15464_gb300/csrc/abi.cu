@@ -1,0 +1,118 @@
+// extern "C" entry points: argument validation, then one launcher call each.
+#include "common.cuh"
+
+namespace tidas {
+int launch_tidas_direct(const float* kern, int taps, int center, bool adjoint, int nz, int nx,
+                        const float* in, float* out, int nf, cudaStream_t st);
+int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int nz, int nx,
+                      const void* in, float* out, int nf, bool resid, cudaStream_t st);
+}  // namespace tidas
+
+using namespace tidas;
+
+static inline cudaStream_t S_(void* s) { return (cudaStream_t)s; }
+
+#define PLAN_OR_FAIL(plan)                                      \
+    TIDAS_REQUIRE(plan != nullptr, "%s: null plan", __func__); \
+    const Plan& P = *(const Plan*)(plan)
+
+extern "C" int das_synthesize(das_plan plan, const double* pos_xz, const float* amp,
+                              int32_t n_scat, int32_t n_frames, void* rf, void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(n_frames >= 1 && n_scat >= 0, "das_synthesize: bad sizes");
+    TIDAS_REQUIRE(rf && (n_scat == 0 || (pos_xz && amp)), "das_synthesize: null pointer");
+    TIDAS_REQUIRE(P.p.n_samples <= 49152, "das_synthesize: n_samples > 49152 unsupported");
+    return launch_synthesize(P, pos_xz, amp, n_scat, n_frames, rf, S_(stream));
+}
+
+extern "C" int das_synthesize_grid(das_plan plan, const float* refl, void* rf, int32_t n_frames,
+                                   void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(n_frames >= 1 && refl && rf, "das_synthesize_grid: bad arguments");
+    TIDAS_REQUIRE(P.p.rf_dtype == TIDAS_RF_F32, "das_synthesize_grid: needs an FP32 plan");
+    TIDAS_REQUIRE(P.p.n_samples <= 49152, "das_synthesize_grid: n_samples > 49152 unsupported");
+    if (P.thalf_samples > kJ - 2)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "pulse longer than %d samples", kJ - 2);
+    return launch_synthesize_grid(P, refl, (float*)rf, n_frames, S_(stream));
+}
+
+extern "C" int das_synthesize_adjoint(das_plan plan, const void* rf, float* refl,
+                                      int32_t n_frames, void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(n_frames >= 1 && refl && rf, "das_synthesize_adjoint: bad arguments");
+    TIDAS_REQUIRE(P.p.rf_dtype == TIDAS_RF_F32, "das_synthesize_adjoint: needs an FP32 plan");
+    if (P.thalf_samples > kJ - 2)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "pulse longer than %d samples", kJ - 2);
+    return launch_synthesize_adjoint(P, (const float*)rf, refl, n_frames, S_(stream));
+}
+
+extern "C" int das_forward(das_plan plan, const void* rf, float* img, int32_t n_frames,
+                           void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(n_frames >= 1 && rf && img, "das_forward: bad arguments");
+    TIDAS_REQUIRE(n_frames <= 65535 * 8, "das_forward: too many frames");
+    return launch_das_forward(P, rf, img, n_frames, S_(stream));
+}
+
+extern "C" int das_adjoint(das_plan plan, const float* img, float* rf, int32_t n_frames,
+                           void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(n_frames >= 1 && rf && img, "das_adjoint: bad arguments");
+    TIDAS_REQUIRE(P.p.rf_dtype == TIDAS_RF_F32, "das_adjoint: needs an FP32 plan");
+    TIDAS_REQUIRE(n_frames <= 65535, "das_adjoint: too many frames");
+    if (P.p.n_samples > 49152)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "das_adjoint: n_samples > 49152");
+    return launch_das_adjoint(P, img, rf, n_frames, S_(stream));
+}
+
+extern "C" int das_delay_table(das_plan plan, int32_t angle, int32_t* idx, float* frac,
+                               void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(idx && frac, "das_delay_table: null pointer");
+    TIDAS_REQUIRE(angle >= 0 && angle < P.p.n_angles, "das_delay_table: bad angle %d", angle);
+    return launch_delay_table(P, angle, idx, frac, S_(stream));
+}
+
+extern "C" int tidas_fit_kernels(das_plan plan, int32_t taps, int32_t ref_stride, float* kernels,
+                                 float* theta, void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(kernels, "tidas_fit_kernels: null kernels");
+    TIDAS_REQUIRE(taps >= 1 && taps <= 255, "tidas_fit_kernels: taps out of range");
+    return launch_fit_kernels(P, taps, ref_stride, kernels, theta, S_(stream));
+}
+
+static int tidas_common(const char* who, const float* kernels, int32_t taps, int32_t nz, int32_t nx,
+                        const void* in, float* out, int32_t n_frames, int32_t variant,
+                        bool adjoint, void* stream) {
+    TIDAS_REQUIRE(kernels && in && out, "%s: null pointer", who);
+    TIDAS_REQUIRE(taps >= 1 && taps <= 255, "%s: taps out of range", who);
+    TIDAS_REQUIRE(nz >= 1 && nz <= 65535 && nx >= 1 && nx <= 16384, "%s: bad grid", who);
+    TIDAS_REQUIRE(n_frames >= 1 && n_frames <= 65535 * 4, "%s: bad frame count", who);
+    const int center = taps / 2;
+    if (variant == TIDAS_VARIANT_DIRECT)
+        return launch_tidas_direct(kernels, taps, center, adjoint, nz, nx, (const float*)in, out,
+                                   n_frames, S_(stream));
+    if (variant == TIDAS_VARIANT_GEMM_BF16 || variant == TIDAS_VARIANT_GEMM_RESID) {
+        TIDAS_REQUIRE(taps <= 63, "%s: GEMM variants need taps <= 63", who);
+        TIDAS_REQUIRE(nx % 8 == 0, "%s: GEMM variants need nx %% 8 == 0", who);
+        TIDAS_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0,
+                      "%s: GEMM variants need 16-byte aligned arrays", who);
+        return launch_tidas_gemm(kernels, taps, center, adjoint, nz, nx, in, out, n_frames,
+                                 variant == TIDAS_VARIANT_GEMM_RESID, S_(stream));
+    }
+    return set_error(TIDAS_ERR_ARG, "%s: unknown variant %d", who, variant);
+}
+
+extern "C" int tidas_forward(const float* kernels, int32_t taps, int32_t nz, int32_t nx,
+                             const void* refl, float* img, int32_t n_frames, int32_t variant,
+                             void* stream) {
+    return tidas_common("tidas_forward", kernels, taps, nz, nx, refl, img, n_frames, variant,
+                        false, stream);
+}
+
+extern "C" int tidas_adjoint(const float* kernels, int32_t taps, int32_t nz, int32_t nx,
+                             const void* img, float* refl, int32_t n_frames, int32_t variant,
+                             void* stream) {
+    return tidas_common("tidas_adjoint", kernels, taps, nz, nx, img, refl, n_frames, variant, true,
+                        stream);
+}

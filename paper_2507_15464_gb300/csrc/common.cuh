@@ -1,0 +1,129 @@
+// Shared host/device helpers of the sm_103a DAS / tiDAS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "tidas.h"
+
+// ---------------------------------------------------------------- errors
+namespace tidas {
+
+int set_error(int code, const char* fmt, ...);
+int check_launch(const char* what);
+int check_cuda(cudaError_t e, const char* what);
+
+#define TIDAS_REQUIRE(cond, ...)                                   \
+    do {                                                           \
+        if (!(cond)) return ::tidas::set_error(TIDAS_ERR_ARG, __VA_ARGS__); \
+    } while (0)
+
+#define TIDAS_CUDA(call)                                           \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::tidas::check_cuda(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------- plan (device view)
+constexpr int kMaxAngles = 16;
+constexpr int kJ = 40;  // pulse tap tables cover j = -kJ..kJ (needs half support < kJ - 1)
+
+// Everything a DAS-family kernel needs, passed by value.
+struct DasDev {
+    int n_elem, n_angles, n_samples, nx, nz, interp, rf_dtype;
+    float fnum;          // <= 0: whole array, unit weights
+    float thalf;         // pulse half support, samples
+    float beta;          // pulse envelope exp(-beta t^2), t in samples
+    float wcar;          // carrier 2 f0 / fs: cos(pi * wcar * t), t in samples
+    // transmit split: u_tx(ix, iz, a) = (bxi + bzi) + (bxf + bzf)   [samples]
+    const int* bxi;      // [A][nx]
+    const float* bxf;    // [A][nx]
+    const int* bzi;      // [A][nz]
+    const float* bzf;    // [A][nz]
+    const float* dxs;    // [n_elem][nx]  (x_ix - x_n) * fs / c
+    const float* zs;     // [nz]          z_iz * fs / c
+    const float* xs;     // [nx]          x_ix * fs / c (grid-free element range search)
+    float elem0_s;       // x_0 * fs / c
+    float pitch_s;       // pitch * fs / c
+    const float* ptab;   // [3][2 kJ + 1]: exp(-beta j^2), cos(pi wcar j), sin(pi wcar j)
+};
+
+// Host-side plan object.
+struct Plan {
+    das_params p;
+    double angles[kMaxAngles];
+    double sn[kMaxAngles], cs[kMaxAngles];
+    DasDev dev;
+    void* blob;             // single device allocation holding every table
+    const double* d_sncs;   // device [A][2]: sin, cos of each angle (host libm values)
+    bool taps_in_range;     // every interpolation tap of every pixel lies in [0, n_samples)
+    double thalf_samples, beta_samples, wcar;
+};
+
+// ---------------------------------------------------------- device helpers
+// Receive correction in samples: sqrt(dx^2 + z^2) - z written without
+// cancellation, dx^2 / (sqrt(dx^2 + z^2) + z).
+__device__ __forceinline__ float rx_excess(float dxs, float zs) {
+    float d2 = dxs * dxs;
+    float s = sqrtf(fmaf(zs, zs, d2));
+    return __fdiv_rn(d2, s + zs);
+}
+
+// Hann receive apodization cos^2(pi r), r = (x - x_n) F# / z, |r| <= 1/2.
+__device__ __forceinline__ float apod_weight(float dxs, float zs, float fnum) {
+    if (fnum <= 0.f) return 1.f;
+    float r = dxs * fnum / zs;
+    if (fabsf(r) > 0.5f) return 0.f;
+    float cw = cospif(r);
+    return cw * cw;
+}
+
+// Keys (a = -0.5) weights of samples i-1, i, i+1, i+2 at fraction phi.
+__device__ __forceinline__ void keys_weights(float phi, float& w0, float& w1, float& w2,
+                                             float& w3) {
+    float p2 = phi * phi;
+    float p3 = p2 * phi;
+    w0 = fmaf(-0.5f, p3, fmaf(1.0f, p2, -0.5f * phi));
+    w1 = fmaf(1.5f, p3, fmaf(-2.5f, p2, 1.0f));
+    w2 = fmaf(-1.5f, p3, fmaf(2.0f, p2, 0.5f * phi));
+    w3 = fmaf(0.5f, p3, -0.5f * p2);
+}
+
+// Split delay of pixel (ix, iz) for angle a and element n:
+// integer sample i and fraction phi in [0, 1).
+__device__ __forceinline__ void pixel_delay(const DasDev& d, int a, int ix, int iz, float excess,
+                                            int& i, float& phi) {
+    int bi = __ldg(d.bxi + a * d.nx + ix) + __ldg(d.bzi + a * d.nz + iz);
+    float bf = __ldg(d.bxf + a * d.nx + ix) + __ldg(d.bzf + a * d.nz + iz);
+    float uf = bf + excess;
+    float fl = floorf(uf);
+    phi = uf - fl;
+    i = bi + (int)fl;
+}
+
+__device__ __forceinline__ float load_rf(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load_rf(const __half* p) { return __half2float(__ldg(p)); }
+
+__device__ __forceinline__ void store_rf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_rf(__half* p, float v) { *p = __float2half_rn(v); }
+
+}  // namespace tidas
+
+// launchers implemented in the .cu files
+namespace tidas {
+int launch_delay_table(const Plan& P, int angle, int32_t* idx, float* frac, cudaStream_t st);
+int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
+int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaStream_t st);
+int launch_synthesize(const Plan& P, const double* pos, const float* amp, int n_scat, int nf,
+                      void* rf, cudaStream_t st);
+int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, cudaStream_t st);
+int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int nf,
+                              cudaStream_t st);
+int launch_fit_kernels(const Plan& P, int taps, int ref_stride, float* kernels, float* theta,
+                       cudaStream_t st);
+int launch_tidas(const float* kernels, int taps, int center, bool flip, int nz, int nx,
+                 const void* in, float* out, int nf, int variant, cudaStream_t st);
+}  // namespace tidas

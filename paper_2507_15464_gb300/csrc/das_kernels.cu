@@ -1,0 +1,573 @@
+// Delay-and-Sum family on CUDA cores (sm_103a): forward DAS (Eq. (2.2)), its
+// transpose, channel-data synthesis (Eq. (2.1)) and its transpose, and the
+// exact single-scatterer PSF rows that define the tiDAS kernels.
+#include "common.cuh"
+
+namespace tidas {
+
+// ---------------------------------------------------------------- DAS
+// One thread per pixel; a warp covers 32 neighbouring columns of one row so
+// that the 32 gathers of one tap fall inside ~32 consecutive samples.  The
+// per-(pixel, element) receive correction and apodization are computed once
+// and reused for every angle; the per-(pixel, element, angle) delay and
+// interpolation weights are reused for the FB frames a thread accumulates.
+template <typename RF, int INTERP, int FB, bool CHECK>
+__global__ void __launch_bounds__(256, 2) das_forward_kernel(DasDev d, const RF* __restrict__ rf,
+                                                             float* __restrict__ img, int nf) {
+    // per-thread transmit delay split of every angle
+    __shared__ int s_bi[kMaxAngles][256];
+    __shared__ float s_bf[kMaxAngles][256];
+    const int lane = threadIdx.x;
+    const int tid = threadIdx.y * 32 + lane;
+    const int ix = blockIdx.x * 32 + lane;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    if (iz >= d.nz) return;  // uniform per warp; no block-wide barrier follows
+    const int f0 = blockIdx.z * FB;
+    const int A = d.n_angles, NE = d.n_elem, S = d.n_samples, NX = d.nx;
+    const bool xin = ix < NX;
+    const int ixc = xin ? ix : NX - 1;
+    const float zs = __ldg(d.zs + iz);
+
+    for (int a = 0; a < A; ++a) {
+        s_bi[a][tid] = __ldg(d.bxi + a * NX + ixc) + __ldg(d.bzi + a * d.nz + iz);
+        s_bf[a][tid] = __ldg(d.bxf + a * NX + ixc) + __ldg(d.bzf + a * d.nz + iz);
+    }
+    __syncwarp();
+
+    // element range of the warp's aperture union (one element of margin)
+    int n_lo = 0, n_hi = NE - 1;
+    if (d.fnum > 0.f) {
+        const int ix_first = blockIdx.x * 32;
+        const int ix_last = min(ix_first + 31, NX - 1);
+        const float h = zs / (2.f * d.fnum);
+        float lo = (__ldg(d.xs + ix_first) - h - d.elem0_s) / d.pitch_s;
+        float hi = (__ldg(d.xs + ix_last) + h - d.elem0_s) / d.pitch_s;
+        n_lo = max(0, (int)floorf(lo) - 1);
+        n_hi = min(NE - 1, (int)ceilf(hi) + 1);
+    }
+
+    float acc[FB];
+#pragma unroll
+    for (int f = 0; f < FB; ++f) acc[f] = 0.f;
+    const size_t fstride = (size_t)A * NE * S;
+
+    for (int n = n_lo; n <= n_hi; ++n) {
+        const float dxs = __ldg(d.dxs + (size_t)n * NX + ixc);
+        const float w = xin ? apod_weight(dxs, zs, d.fnum) : 0.f;
+        if (__ballot_sync(0xffffffffu, w != 0.f) == 0u) continue;
+        const float exc = rx_excess(dxs, zs);
+#pragma unroll 2
+        for (int a = 0; a < A; ++a) {
+            const float uf = s_bf[a][tid] + exc;
+            const float fl = floorf(uf);
+            const float phi = uf - fl;
+            const int i = s_bi[a][tid] + (int)fl;
+            const RF* row = rf + ((size_t)(f0 * A + a) * NE + n) * S;
+            if (INTERP == TIDAS_INTERP_CUBIC) {
+                float w0, w1, w2, w3;
+                keys_weights(phi, w0, w1, w2, w3);
+                int m0 = i - 1, m1 = i, m2 = i + 1, m3 = i + 2;
+                if (CHECK) {
+                    if ((unsigned)m0 >= (unsigned)S) { w0 = 0.f; m0 = 0; }
+                    if ((unsigned)m1 >= (unsigned)S) { w1 = 0.f; m1 = 0; }
+                    if ((unsigned)m2 >= (unsigned)S) { w2 = 0.f; m2 = 0; }
+                    if ((unsigned)m3 >= (unsigned)S) { w3 = 0.f; m3 = 0; }
+                }
+#pragma unroll
+                for (int f = 0; f < FB; ++f) {
+                    if (FB > 1 && f0 + f >= nf) break;
+                    const RF* r = row + f * fstride;
+                    float v = w0 * load_rf(r + m0);
+                    v = fmaf(w1, load_rf(r + m1), v);
+                    v = fmaf(w2, load_rf(r + m2), v);
+                    v = fmaf(w3, load_rf(r + m3), v);
+                    acc[f] = fmaf(w, v, acc[f]);
+                }
+            } else {
+                float w0 = 1.f - phi, w1 = phi;
+                int m0 = i, m1 = i + 1;
+                if (CHECK) {
+                    if ((unsigned)m0 >= (unsigned)S) { w0 = 0.f; m0 = 0; }
+                    if ((unsigned)m1 >= (unsigned)S) { w1 = 0.f; m1 = 0; }
+                }
+#pragma unroll
+                for (int f = 0; f < FB; ++f) {
+                    if (FB > 1 && f0 + f >= nf) break;
+                    const RF* r = row + f * fstride;
+                    float v = w0 * load_rf(r + m0);
+                    v = fmaf(w1, load_rf(r + m1), v);
+                    acc[f] = fmaf(w, v, acc[f]);
+                }
+            }
+        }
+    }
+    if (xin) {
+#pragma unroll
+        for (int f = 0; f < FB; ++f)
+            if (f0 + f < nf) img[((size_t)(f0 + f) * d.nz + iz) * NX + ix] = acc[f];
+    }
+}
+
+template <typename RF, int INTERP, bool CHECK>
+static void das_forward_dispatch_fb(const DasDev& d, const void* rf, float* img, int nf,
+                                    cudaStream_t st) {
+    dim3 block(32, 8);
+    int fb = nf >= 8 ? 8 : (nf >= 4 ? 4 : (nf >= 2 ? 2 : 1));
+    dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, (nf + fb - 1) / fb);
+    const RF* r = (const RF*)rf;
+    switch (fb) {
+        case 8: das_forward_kernel<RF, INTERP, 8, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
+        case 4: das_forward_kernel<RF, INTERP, 4, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
+        case 2: das_forward_kernel<RF, INTERP, 2, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
+        default: das_forward_kernel<RF, INTERP, 1, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
+    }
+}
+
+template <typename RF>
+static void das_forward_dispatch(const Plan& P, const void* rf, float* img, int nf,
+                                 cudaStream_t st) {
+    const DasDev& d = P.dev;
+    bool check = !P.taps_in_range;
+    if (d.interp == TIDAS_INTERP_CUBIC) {
+        if (check) das_forward_dispatch_fb<RF, 1, true>(d, rf, img, nf, st);
+        else das_forward_dispatch_fb<RF, 1, false>(d, rf, img, nf, st);
+    } else {
+        if (check) das_forward_dispatch_fb<RF, 0, true>(d, rf, img, nf, st);
+        else das_forward_dispatch_fb<RF, 0, false>(d, rf, img, nf, st);
+    }
+}
+
+int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st) {
+    if (P.dev.rf_dtype == TIDAS_RF_F16) das_forward_dispatch<__half>(P, rf, img, nf, st);
+    else das_forward_dispatch<float>(P, rf, img, nf, st);
+    return check_launch("das_forward_kernel");
+}
+
+// ------------------------------------------------------------ DAS^T
+// One block per (element, angle, frame) channel row, accumulated in shared
+// memory.  Threads walk the rows of each column (their delays are ~3 samples
+// apart, so taps of neighbouring lanes rarely collide) and add
+// w * (interpolation weight) * img into the samples the forward pass read.
+template <int INTERP>
+__global__ void __launch_bounds__(256) das_adjoint_kernel(DasDev d, const float* __restrict__ img,
+                                                          float* __restrict__ rf) {
+    extern __shared__ float acc[];
+    const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
+    const int S = d.n_samples, NX = d.nx, NZ = d.nz;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) acc[k] = 0.f;
+    __syncthreads();
+    const float* im = img + (size_t)f * NZ * NX;
+    for (int ix = 0; ix < NX; ++ix) {
+        const float dxs = __ldg(d.dxs + (size_t)n * NX + ix);
+        for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+            const float zs = __ldg(d.zs + iz);
+            const float w = apod_weight(dxs, zs, d.fnum);
+            if (w == 0.f) continue;
+            const float exc = rx_excess(dxs, zs);
+            int i;
+            float phi;
+            pixel_delay(d, a, ix, iz, exc, i, phi);
+            const float v = w * __ldg(im + (size_t)iz * NX + ix);
+            if (INTERP == TIDAS_INTERP_CUBIC) {
+                float w0, w1, w2, w3;
+                keys_weights(phi, w0, w1, w2, w3);
+                if ((unsigned)(i - 1) < (unsigned)S) atomicAdd(acc + i - 1, w0 * v);
+                if ((unsigned)(i) < (unsigned)S) atomicAdd(acc + i, w1 * v);
+                if ((unsigned)(i + 1) < (unsigned)S) atomicAdd(acc + i + 1, w2 * v);
+                if ((unsigned)(i + 2) < (unsigned)S) atomicAdd(acc + i + 2, w3 * v);
+            } else {
+                if ((unsigned)(i) < (unsigned)S) atomicAdd(acc + i, (1.f - phi) * v);
+                if ((unsigned)(i + 1) < (unsigned)S) atomicAdd(acc + i + 1, phi * v);
+            }
+        }
+    }
+    __syncthreads();
+    float* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) out[k] = acc[k];
+}
+
+int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaStream_t st) {
+    const DasDev& d = P.dev;
+    size_t smem = (size_t)d.n_samples * sizeof(float);
+    dim3 grid(d.n_elem, d.n_angles, nf);
+    if (d.interp == TIDAS_INTERP_CUBIC) {
+        cudaFuncSetAttribute(das_adjoint_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        das_adjoint_kernel<1><<<grid, 256, smem, st>>>(d, img, rf);
+    } else {
+        cudaFuncSetAttribute(das_adjoint_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        das_adjoint_kernel<0><<<grid, 256, smem, st>>>(d, img, rf);
+    }
+    return check_launch("das_adjoint_kernel");
+}
+
+// --------------------------------------------------------------- pulse
+// Taps of the pulse delayed by a fractional sample phi: p(j - phi) for the
+// integers j with |j - phi| <= thalf, p(t) = exp(-beta t^2) cos(pi wcar t).
+// Written as exp(-beta phi^2) * Q_j * G^j * (C_j cos(pi wcar phi) +
+// S_j sin(pi wcar phi)) with Q_j = exp(-beta j^2), G = exp(2 beta phi),
+// C_j + i S_j = exp(i pi wcar j): one exp pair and one sincos per delay,
+// then a few multiplies per tap.  Tables live in shared memory (index j + kJ).
+struct PulseSmem {
+    float q[2 * kJ + 1], c[2 * kJ + 1], s[2 * kJ + 1];
+};
+
+__device__ void load_pulse_tables(const DasDev& d, PulseSmem& t) {
+    for (int j = threadIdx.x + threadIdx.y * blockDim.x; j <= 2 * kJ;
+         j += blockDim.x * blockDim.y) {
+        t.q[j] = __ldg(d.ptab + j);
+        t.c[j] = __ldg(d.ptab + (2 * kJ + 1) + j);
+        t.s[j] = __ldg(d.ptab + 2 * (2 * kJ + 1) + j);
+    }
+}
+
+struct PulseAt {
+    float e0, g, ginv, cph, sph;
+    int jlo, jhi;
+};
+
+__device__ __forceinline__ PulseAt pulse_at(const DasDev& d, float phi) {
+    PulseAt p;
+    p.e0 = expf(-d.beta * phi * phi);
+    p.g = expf(2.f * d.beta * phi);
+    p.ginv = expf(-2.f * d.beta * phi);
+    sincospif(d.wcar * phi, &p.sph, &p.cph);
+    p.jlo = (int)ceilf(phi - d.thalf);
+    p.jhi = (int)floorf(phi + d.thalf);
+    return p;
+}
+
+// ------------------------------------------------- synthesis, point list
+// One block per (element, angle, frame) channel row; scatterers are spread
+// over the threads; samples accumulate in shared memory.  Delays in FP64.
+template <typename RF>
+__global__ void __launch_bounds__(256) synth_points_kernel(DasDev d, const double* __restrict__ pos,
+                                                           const float* __restrict__ amp, int n_scat,
+                                                           const double* __restrict__ sncs,
+                                                           RF* __restrict__ rf, double c, double t0,
+                                                           double fs, double pitch) {
+    extern __shared__ float acc[];
+    const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
+    const int S = d.n_samples;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) acc[k] = 0.f;
+    __syncthreads();
+    const double sa = sncs[2 * a], ca = sncs[2 * a + 1];
+    const double xn = __dmul_rn(__dsub_rn((double)n, 0.5 * (double)(d.n_elem - 1)), pitch);
+    const double* ps = pos + (size_t)f * n_scat * 2;
+    const float* am = amp + (size_t)f * n_scat * 2;
+    for (int j = threadIdx.x; j < n_scat; j += blockDim.x) {
+        const double x = ps[2 * j], z = ps[2 * j + 1];
+        const double ddx = __dsub_rn(x, xn);
+        const double tx = __dadd_rn(__dmul_rn(x, sa), __dmul_rn(z, ca));
+        const double rx = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(z, z)));
+        const double u = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn(tx, rx), c), t0), fs);
+        const double fl = floor(u);
+        const int i0 = (int)fl;
+        const float phi = (float)(u - fl);
+        const float are = am[2 * j], aim = am[2 * j + 1];
+        const int jlo = (int)ceilf(phi - d.thalf), jhi = (int)floorf(phi + d.thalf);
+        for (int jj = jlo; jj <= jhi; ++jj) {
+            const int m = i0 + jj;
+            if ((unsigned)m >= (unsigned)S) continue;
+            const float t = (float)jj - phi;
+            float sv, cv;
+            sincospif(d.wcar * t, &sv, &cv);
+            const float env = expf(-d.beta * t * t);
+            atomicAdd(acc + m, env * (are * cv - aim * sv));
+        }
+    }
+    __syncthreads();
+    RF* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) store_rf(out + k, acc[k]);
+}
+
+int launch_synthesize(const Plan& P, const double* pos, const float* amp, int n_scat, int nf,
+                      void* rf, cudaStream_t st) {
+    const DasDev& d = P.dev;
+    size_t smem = (size_t)d.n_samples * sizeof(float);
+    dim3 grid(d.n_elem, d.n_angles, nf);
+    if (d.rf_dtype == TIDAS_RF_F16) {
+        cudaFuncSetAttribute(synth_points_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        synth_points_kernel<__half><<<grid, 256, smem, st>>>(d, pos, amp, n_scat, P.d_sncs,
+                                                            (__half*)rf, P.p.c, P.p.t0, P.p.fs,
+                                                            P.p.pitch);
+    } else {
+        cudaFuncSetAttribute(synth_points_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        synth_points_kernel<float><<<grid, 256, smem, st>>>(d, pos, amp, n_scat, P.d_sncs,
+                                                           (float*)rf, P.p.c, P.p.t0, P.p.fs,
+                                                           P.p.pitch);
+    }
+    return check_launch("synth_points_kernel");
+}
+
+// ------------------------------------------------- synthesis on the grid
+// Same row-per-block scheme; the "scatterers" are the pixels, with the split
+// delays of DAS, so that this operator and its transpose below use
+// identical delays and pulse taps.
+__global__ void __launch_bounds__(256) synth_grid_kernel(DasDev d, const float* __restrict__ refl,
+                                                         float* __restrict__ rf) {
+    extern __shared__ float acc[];
+    __shared__ PulseSmem tab;
+    const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
+    const int S = d.n_samples, NX = d.nx, NZ = d.nz;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) acc[k] = 0.f;
+    load_pulse_tables(d, tab);
+    __syncthreads();
+    const float* rp = refl + (size_t)f * NZ * NX;
+    for (int ix = 0; ix < NX; ++ix) {
+        const float dxs = __ldg(d.dxs + (size_t)n * NX + ix);
+        for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+            const float v = __ldg(rp + (size_t)iz * NX + ix);
+            if (v == 0.f) continue;
+            const float zs = __ldg(d.zs + iz);
+            int i;
+            float phi;
+            pixel_delay(d, a, ix, iz, rx_excess(dxs, zs), i, phi);
+            const PulseAt p = pulse_at(d, phi);
+            const float ve = v * p.e0;
+            float gj = 1.f;
+            for (int j = 0; j <= p.jhi; ++j) {
+                const int m = i + j;
+                if ((unsigned)m < (unsigned)S) {
+                    float car = fmaf(tab.c[j + kJ], p.cph, tab.s[j + kJ] * p.sph);
+                    atomicAdd(acc + m, ve * (tab.q[j + kJ] * gj) * car);
+                }
+                gj *= p.g;
+            }
+            gj = p.ginv;
+            for (int j = -1; j >= p.jlo; --j) {
+                const int m = i + j;
+                if ((unsigned)m < (unsigned)S) {
+                    float car = fmaf(tab.c[j + kJ], p.cph, tab.s[j + kJ] * p.sph);
+                    atomicAdd(acc + m, ve * (tab.q[j + kJ] * gj) * car);
+                }
+                gj *= p.ginv;
+            }
+        }
+    }
+    __syncthreads();
+    float* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) out[k] = acc[k];
+}
+
+int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, cudaStream_t st) {
+    const DasDev& d = P.dev;
+    size_t smem = (size_t)d.n_samples * sizeof(float);
+    cudaFuncSetAttribute(synth_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    synth_grid_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem, st>>>(d, refl, rf);
+    return check_launch("synth_grid_kernel");
+}
+
+// ------------------------------------------------ synthesis transpose
+// One thread per pixel: correlate every channel row with the pulse delayed
+// to the pixel's round-trip time.  Same taps as synth_grid_kernel.
+__global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const float* __restrict__ rf,
+                                                            float* __restrict__ refl) {
+    __shared__ PulseSmem tab;
+    load_pulse_tables(d, tab);
+    __syncthreads();
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    const int f = blockIdx.z;
+    if (ix >= d.nx || iz >= d.nz) return;
+    const int S = d.n_samples, NE = d.n_elem, A = d.n_angles;
+    const float zs = __ldg(d.zs + iz);
+    float acc = 0.f;
+    for (int n = 0; n < NE; ++n) {
+        const float exc = rx_excess(__ldg(d.dxs + (size_t)n * d.nx + ix), zs);
+        for (int a = 0; a < A; ++a) {
+            int i;
+            float phi;
+            pixel_delay(d, a, ix, iz, exc, i, phi);
+            const float* row = rf + ((size_t)(f * A + a) * NE + n) * S;
+            const PulseAt p = pulse_at(d, phi);
+            float s = 0.f, gj = 1.f;
+            for (int j = 0; j <= p.jhi; ++j) {
+                const int m = i + j;
+                if ((unsigned)m < (unsigned)S) {
+                    float car = fmaf(tab.c[j + kJ], p.cph, tab.s[j + kJ] * p.sph);
+                    s = fmaf(__ldg(row + m), (tab.q[j + kJ] * gj) * car, s);
+                }
+                gj *= p.g;
+            }
+            gj = p.ginv;
+            for (int j = -1; j >= p.jlo; --j) {
+                const int m = i + j;
+                if ((unsigned)m < (unsigned)S) {
+                    float car = fmaf(tab.c[j + kJ], p.cph, tab.s[j + kJ] * p.sph);
+                    s = fmaf(__ldg(row + m), (tab.q[j + kJ] * gj) * car, s);
+                }
+                gj *= p.ginv;
+            }
+            acc = fmaf(p.e0, s, acc);
+        }
+    }
+    refl[((size_t)f * d.nz + iz) * d.nx + ix] = acc;
+}
+
+int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int nf,
+                              cudaStream_t st) {
+    const DasDev& d = P.dev;
+    dim3 block(32, 8);
+    dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, nf);
+    synth_adjoint_kernel<<<grid, block, 0, st>>>(d, rf, refl);
+    return check_launch("synth_adjoint_kernel");
+}
+
+// ------------------------------------------------------- PSF / kernel fit
+// Exact single-scatterer PSF (Eq. (2.6)-(2.7)): the DAS value at pixel
+// (ic + t - taps/2, iz) of a unit scatterer on pixel (ic, iz), without
+// materialising channel data: the beamformer reads the sampled pulse
+// p(m - u_scat) at the interpolation taps m around u_pix.  Delays in FP64.
+struct FitArgs {
+    int n_elem, n_angles, nx, nz, taps, ic, interp, n_samples;
+    double pitch, c, fs, t0, x0, dx, z0, dz, fnum;
+    double thalf, beta, wcar;  // samples
+};
+
+__device__ __forceinline__ double delay_fp64(const FitArgs& A, double sn, double cs, int n,
+                                             double x, double z) {
+    double xn = __dmul_rn(__dsub_rn((double)n, 0.5 * (double)(A.n_elem - 1)), A.pitch);
+    double ddx = __dsub_rn(x, xn);
+    double tx = __dadd_rn(__dmul_rn(x, sn), __dmul_rn(z, cs));
+    double rx = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(z, z)));
+    return __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn(tx, rx), A.c), A.t0), A.fs);
+}
+
+__device__ __forceinline__ double pulse_fp(const FitArgs& A, double t) {
+    if (fabs(t) > A.thalf) return 0.0;
+    float tf = (float)t;
+    return (double)(expf(-(float)A.beta * tf * tf) * cospif((float)A.wcar * tf));
+}
+
+__global__ void fit_psf_kernel(FitArgs A, const double* __restrict__ sncs, float* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y;
+    if (t >= A.taps) return;
+    const int ix = A.ic + t - A.taps / 2;
+    float result = 0.f;
+    if (ix >= 0 && ix < A.nx) {
+        const double z = A.z0 + ((double)iz + 0.5) * A.dz;
+        const double xs = A.x0 + ((double)A.ic + 0.5) * A.dx;  // scatterer
+        const double xp = A.x0 + ((double)ix + 0.5) * A.dx;    // pixel
+        double acc = 0.0;
+        for (int a = 0; a < A.n_angles; ++a) {
+            const double sn = sncs[2 * a], cs = sncs[2 * a + 1];
+            for (int n = 0; n < A.n_elem; ++n) {
+                double w = 1.0;
+                if (A.fnum > 0) {
+                    double xn = ((double)n - 0.5 * (double)(A.n_elem - 1)) * A.pitch;
+                    double r = (xp - xn) * A.fnum / z;
+                    if (fabs(r) > 0.5) continue;
+                    double cw = cospi(r);
+                    w = cw * cw;
+                }
+                const double up = delay_fp64(A, sn, cs, n, xp, z);
+                const double us = delay_fp64(A, sn, cs, n, xs, z);
+                const double fl = floor(up);
+                const double phi = up - fl;
+                const int i = (int)fl;
+                double v = 0.0;
+                if (A.interp == TIDAS_INTERP_CUBIC) {
+                    float w0, w1, w2, w3;
+                    keys_weights((float)phi, w0, w1, w2, w3);
+                    const float wt[4] = {w0, w1, w2, w3};
+                    for (int k = 0; k < 4; ++k) {
+                        const int m = i - 1 + k;
+                        if (m < 0 || m >= A.n_samples) continue;
+                        v += (double)wt[k] * pulse_fp(A, (double)m - us);
+                    }
+                } else {
+                    if (i >= 0 && i < A.n_samples) v += (1.0 - phi) * pulse_fp(A, (double)i - us);
+                    if (i + 1 >= 0 && i + 1 < A.n_samples)
+                        v += phi * pulse_fp(A, (double)(i + 1) - us);
+                }
+                acc += w * v;
+            }
+        }
+        result = (float)acc;
+    }
+    out[(size_t)iz * A.taps + t] = result;
+}
+
+// Rows other than the reference rows become theta * (reference PSF), with
+// theta the least-squares weight of Eq. (2.12); reference rows are only read.
+__global__ void fit_theta_kernel(int nz, int taps, int ref_stride, float* __restrict__ kern,
+                                 float* __restrict__ theta) {
+    const int iz = blockIdx.x;
+    int s = (iz / ref_stride) * ref_stride + ref_stride / 2;
+    if (s > nz - 1) s = nz - 1;
+    if (iz == s) {
+        if (theta && threadIdx.x == 0) theta[iz] = 1.f;
+        return;
+    }
+    __shared__ double red_ab[256], red_aa[256];
+    double ab = 0.0, aa = 0.0;
+    for (int t = threadIdx.x; t < taps; t += blockDim.x) {
+        double a = kern[(size_t)s * taps + t], b = kern[(size_t)iz * taps + t];
+        ab += a * b;
+        aa += a * a;
+    }
+    red_ab[threadIdx.x] = ab;
+    red_aa[threadIdx.x] = aa;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            red_ab[threadIdx.x] += red_ab[threadIdx.x + k];
+            red_aa[threadIdx.x] += red_aa[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    const double th = red_aa[0] > 0 ? red_ab[0] / red_aa[0] : 0.0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < taps; t += blockDim.x)
+        kern[(size_t)iz * taps + t] = (float)(th * (double)kern[(size_t)s * taps + t]);
+    if (theta && threadIdx.x == 0) theta[iz] = (float)th;
+}
+
+__global__ void fill_ones_kernel(float* p, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 1.f;
+}
+
+int launch_fit_kernels(const Plan& P, int taps, int ref_stride, float* kernels, float* theta,
+                       cudaStream_t st) {
+    FitArgs A;
+    A.n_elem = P.p.n_elem;
+    A.n_angles = P.p.n_angles;
+    A.nx = P.p.nx;
+    A.nz = P.p.nz;
+    A.taps = taps;
+    A.ic = P.p.nx / 2;
+    A.interp = P.p.interp;
+    A.n_samples = P.p.n_samples;
+    A.pitch = P.p.pitch;
+    A.c = P.p.c;
+    A.fs = P.p.fs;
+    A.t0 = P.p.t0;
+    A.x0 = P.p.x0;
+    A.dx = P.p.dx;
+    A.z0 = P.p.z0;
+    A.dz = P.p.dz;
+    A.fnum = P.p.fnum;
+    A.thalf = P.thalf_samples;
+    A.beta = P.beta_samples;
+    A.wcar = P.wcar;
+    dim3 grid((taps + 63) / 64, P.p.nz);
+    fit_psf_kernel<<<grid, 64, 0, st>>>(A, P.d_sncs, kernels);
+    int rc = check_launch("fit_psf_kernel");
+    if (rc) return rc;
+    if (ref_stride > 1) {
+        fit_theta_kernel<<<P.p.nz, 256, 0, st>>>(P.p.nz, taps, ref_stride, kernels, theta);
+        rc = check_launch("fit_theta_kernel");
+    } else if (theta) {
+        fill_ones_kernel<<<(P.p.nz + 255) / 256, 256, 0, st>>>(theta, P.p.nz);
+        rc = check_launch("fill_ones_kernel");
+    }
+    return rc;
+}
+
+}  // namespace tidas

@@ -1,0 +1,150 @@
+"""Torch-facing wrappers: allocate outputs as CUDA tensors, pass pointers and the
+current stream to the C ABI.  Every operation runs in libtidas.so kernels;
+torch only supplies device memory and streams.
+"""
+import ctypes
+import math
+
+import torch
+
+from . import capi
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _need(t, dtype, shape, name):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError("%s: expected %s %s, got %s %s" % (name, dtype, tuple(shape), t.dtype,
+                                                            tuple(t.shape)))
+
+
+class DasPlan:
+    """A das_plan for one geometry dict (tidas_workloads.presets form)."""
+
+    def __init__(self, geom: dict, rf_dtype=torch.float32):
+        self.geom = dict(geom)
+        ang = geom.get("angles_rad")
+        if ang is None:
+            ang = [a * math.pi / 180.0 for a in geom["angles_deg"]]
+        self._angles = (ctypes.c_double * len(ang))(*ang)
+        p = capi.das_params()
+        for k in ("n_elem", "n_samples", "nx", "nz", "interp"):
+            setattr(p, k, int(geom[k]))
+        for k in ("pitch", "f0", "fs", "c", "frac_bw", "t0", "x0", "dx", "z0", "dz", "fnum"):
+            setattr(p, k, float(geom[k]))
+        p.n_angles = len(ang)
+        p.angles_rad = ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double))
+        if rf_dtype not in (torch.float32, torch.float16):
+            raise ValueError("rf_dtype must be float32 or float16")
+        p.rf_dtype = capi.RF_F16 if rf_dtype == torch.float16 else capi.RF_F32
+        self.rf_dtype = rf_dtype
+        self.params = p
+        self.handle = capi.das_plan_create(p)
+        self.A, self.N, self.S = p.n_angles, p.n_elem, p.n_samples
+        self.nx, self.nz = p.nx, p.nz
+
+    def close(self):
+        if self.handle:
+            capi.das_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes
+    def rf_shape(self, nf):
+        return (nf, self.A, self.N, self.S)
+
+    def img_shape(self, nf):
+        return (nf, self.nz, self.nx)
+
+    # operations
+    def synthesize(self, pos, amp, out=None):
+        """pos [B, n, 2] float64, amp [B, n, 2] float32 (CUDA) -> rf [B, A, N, S]."""
+        nf, n = pos.shape[0], pos.shape[1]
+        _need(pos, torch.float64, (nf, n, 2), "pos")
+        _need(amp, torch.float32, (nf, n, 2), "amp")
+        out = out if out is not None else torch.empty(self.rf_shape(nf), dtype=self.rf_dtype,
+                                                      device=pos.device)
+        capi.das_synthesize(self.handle, _ptr(pos), _ptr(amp), n, nf, _ptr(out), _stream())
+        return out
+
+    def synthesize_grid(self, refl, out=None):
+        nf = refl.shape[0]
+        _need(refl, torch.float32, self.img_shape(nf), "refl")
+        out = out if out is not None else torch.empty(self.rf_shape(nf), dtype=torch.float32,
+                                                      device=refl.device)
+        capi.das_synthesize_grid(self.handle, _ptr(refl), _ptr(out), nf, _stream())
+        return out
+
+    def synthesize_adjoint(self, rf, out=None):
+        nf = rf.shape[0]
+        _need(rf, torch.float32, self.rf_shape(nf), "rf")
+        out = out if out is not None else torch.empty(self.img_shape(nf), dtype=torch.float32,
+                                                      device=rf.device)
+        capi.das_synthesize_adjoint(self.handle, _ptr(rf), _ptr(out), nf, _stream())
+        return out
+
+    def forward(self, rf, out=None):
+        nf = rf.shape[0]
+        _need(rf, self.rf_dtype, self.rf_shape(nf), "rf")
+        out = out if out is not None else torch.empty(self.img_shape(nf), dtype=torch.float32,
+                                                      device=rf.device)
+        capi.das_forward(self.handle, _ptr(rf), _ptr(out), nf, _stream())
+        return out
+
+    def adjoint(self, img, out=None):
+        nf = img.shape[0]
+        _need(img, torch.float32, self.img_shape(nf), "img")
+        out = out if out is not None else torch.empty(self.rf_shape(nf), dtype=torch.float32,
+                                                      device=img.device)
+        capi.das_adjoint(self.handle, _ptr(img), _ptr(out), nf, _stream())
+        return out
+
+    def delay_table(self, angle, device="cuda"):
+        idx = torch.empty((self.nz, self.nx, self.N), dtype=torch.int32, device=device)
+        frac = torch.empty((self.nz, self.nx, self.N), dtype=torch.float32, device=device)
+        capi.das_delay_table(self.handle, angle, _ptr(idx), _ptr(frac), _stream())
+        return idx, frac
+
+    def fit_kernels(self, taps, ref_stride=1, device="cuda"):
+        k = torch.empty((self.nz, taps), dtype=torch.float32, device=device)
+        th = torch.empty((self.nz,), dtype=torch.float32, device=device)
+        capi.tidas_fit_kernels(self.handle, taps, ref_stride, _ptr(k), _ptr(th), _stream())
+        return k, th
+
+
+def _tidas(fn, kernels, x, variant, out=None):
+    nz, taps = kernels.shape
+    nf, nz2, nx = x.shape
+    if nz2 != nz:
+        raise ValueError("kernel rows and image rows differ")
+    _need(kernels, torch.float32, (nz, taps), "kernels")
+    want = torch.bfloat16 if variant == capi.VARIANT_GEMM_BF16 else torch.float32
+    _need(x, want, (nf, nz, nx), "input")
+    out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
+                                                  device=x.device)
+    fn(_ptr(kernels), taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
+    return out
+
+
+def tidas_forward(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
+    """Eq. (2.13) row-wise lateral convolution: refl [B, nz, nx] -> img [B, nz, nx]."""
+    return _tidas(capi.tidas_forward, kernels, refl, variant, out)
+
+
+def tidas_adjoint(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
+    return _tidas(capi.tidas_adjoint, kernels, img, variant, out)

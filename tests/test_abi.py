@@ -1,0 +1,91 @@
+"""CPU-only checks of the C ABI boundary: the library builds, loads without a
+GPU and exports every function include/tidas.h declares; host-side argument
+validation rejects bad plans before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2507_15464_gb300 import capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("das_plan_create", "das_forward", "das_adjoint", "tidas_fit_kernels",
+                 "tidas_forward", "tidas_adjoint", "tidas_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = capi.load()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(capi.EXPORTED) <= set(declared_functions())
+
+
+def test_params_struct_layout_matches_header():
+    # the ctypes mirror must follow the header's field order
+    text = open(os.path.join(ROOT, "include", "tidas.h")).read()
+    body = text[text.index("typedef struct {") + len("typedef struct {"):text.index("} das_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    flat = re.findall(r"(\w+)\s*[,;]", body)
+    assert flat == [f[0] for f in capi.das_params._fields_]
+
+
+def _params(**kw):
+    p = capi.das_params()
+    ang = (ctypes.c_double * 1)(0.0)
+    vals = dict(n_elem=8, pitch=3e-4, f0=5e6, fs=4e7, c=1540.0, frac_bw=0.6, n_angles=1,
+                n_samples=256, t0=0.0, nx=8, nz=8, x0=-1e-3, dx=2.5e-4, z0=5e-3, dz=2.5e-4,
+                interp=1, fnum=1.5, rf_dtype=0)
+    vals.update(kw)
+    for k, v in vals.items():
+        setattr(p, k, v)
+    p.angles_rad = ctypes.cast(ang, ctypes.POINTER(ctypes.c_double))
+    return p, ang
+
+
+@pytest.mark.parametrize("bad", [dict(n_elem=0), dict(n_angles=17), dict(nx=0), dict(c=-1.0),
+                                 dict(interp=3), dict(rf_dtype=7), dict(z0=-1.0),
+                                 dict(frac_bw=0.0), dict(n_samples=2)])
+def test_plan_rejects_bad_parameters(bad):
+    p, keep = _params(**bad)
+    with pytest.raises(capi.TidasError) as e:
+        capi.das_plan_create(p)
+    assert e.value.code == capi.TIDAS_ERR_ARG
+    assert capi.tidas_last_error()
+
+
+def test_null_arguments_are_rejected_before_any_launch():
+    with pytest.raises(capi.TidasError) as e:
+        capi.das_forward(None, 1, 1, 1)
+    assert e.value.code == capi.TIDAS_ERR_ARG
+    with pytest.raises(capi.TidasError) as e:
+        capi.tidas_forward(None, 31, 8, 8, 1, 1, 1, 0)
+    assert e.value.code == capi.TIDAS_ERR_ARG
+    with pytest.raises(capi.TidasError) as e:  # unknown variant
+        capi.tidas_forward(16, 31, 8, 8, 16, 16, 1, 9)
+    assert e.value.code == capi.TIDAS_ERR_ARG
+    with pytest.raises(capi.TidasError) as e:  # GEMM needs taps <= 63
+        capi.tidas_forward(16, 65, 8, 8, 16, 16, 1, capi.VARIANT_GEMM_BF16)
+    assert e.value.code == capi.TIDAS_ERR_ARG
+    with pytest.raises(capi.TidasError) as e:  # GEMM needs 16-byte alignment
+        capi.tidas_forward(16, 63, 8, 8, 18, 16, 1, capi.VARIANT_GEMM_BF16)
+    assert e.value.code == capi.TIDAS_ERR_ARG
