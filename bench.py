@@ -1,0 +1,400 @@
+"""Throughput benchmark: exact compounded-plane-wave DAS (and tiDAS beside it)
+on one GB300, in Mpixels/s, with roofline fractions and the FP64 CPU oracle
+timed on the host cores in the same run.
+
+Workload: 128-element linear array, 11 plane waves (-10..+10 deg), 4096
+samples per channel, 512 x 1024 pixel grid, cubic interpolation, F# 1.5;
+64 frames of FP16 channel data synthesised from 100k complex-Gaussian speckle
+scatterers plus 10 bright targets per frame.  One step = das_forward over the
+64-frame batch (inputs resident in HBM; the 738 MB batch exceeds the 129 MB
+L2, so every step streams it from HBM).  tiDAS is timed on 256 frames of
+1024 x 512 sparse reflectivity with 63-tap kernels fitted from the same
+geometry.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixels/s exact DAS vs tiDAS on 1 GB300 at stated NRMSE vs FP64 oracle; % HBM/tensor peak"
+GEOM = "pw128_compound"
+BATCH = 64
+TIDAS_FRAMES = 256
+TAPS = 63
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tidas", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- workload bits
+def active_updates(g):
+    """Exact count of (pixel, element) pairs inside the F# aperture, times angles."""
+    from tidas_workloads.presets import angles_rad
+    xs = g["x0"] + (np.arange(g["nx"]) + 0.5) * g["dx"]
+    zs = g["z0"] + (np.arange(g["nz"]) + 0.5) * g["dz"]
+    xn = (np.arange(g["n_elem"]) - 0.5 * (g["n_elem"] - 1)) * g["pitch"]
+    cnt = 0
+    for z in zs:
+        r = np.abs(xs[:, None] - xn[None, :]) * g["fnum"] / z
+        cnt += int(np.count_nonzero(r <= 0.5))
+    return cnt * len(angles_rad(g))
+
+
+def make_rf(plan, torch, nf, seed_base=1):
+    """Synthesise nf frames of channel data on the GPU (speckle + targets)."""
+    from tidas_workloads import generators
+    rf = torch.empty(plan.rf_shape(nf), dtype=plan.rf_dtype, device="cuda")
+    chunk = 8
+    for f0 in range(0, nf, chunk):
+        fs = list(range(f0, min(nf, f0 + chunk)))
+        ps, am = zip(*[generators.compound_speckle_frame(f, seed=seed_base) for f in fs])
+        pos = torch.from_numpy(np.stack(ps)).cuda()
+        amp = torch.from_numpy(np.stack(am)).cuda()
+        plan.synthesize(pos, amp, out=rf[f0:f0 + len(fs)])
+    torch.cuda.synchronize()
+    return rf
+
+
+def time_steps(torch, fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / steps  # ms per step
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_das_sample(g, rf_host_frame, seconds=10.0):
+    """Time the FP64 oracle on sampled pixels of one frame; returns
+    (Mpixels/s, pixels timed, threads)."""
+    import oracle
+    O = oracle.Oracle(g)
+    rf64 = rf_host_frame.astype(np.float64)
+    rng = np.random.default_rng(0)
+    npx = 512
+    t0 = time.perf_counter()
+    O.das_pixels(rf64, rng.choice(g["nx"] * g["nz"], npx, replace=False))
+    dt = time.perf_counter() - t0
+    npx = int(min(g["nx"] * g["nz"], max(512, npx * seconds / max(dt, 1e-3))))
+    pix = rng.choice(g["nx"] * g["nz"], npx, replace=False)
+    t0 = time.perf_counter()
+    O.das_pixels(rf64, pix)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return npx / dt / 1e6, npx, threads
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2507_15464_gb300 import capi, ops
+    from tidas_workloads import presets, generators
+
+    hbm_peak, bf16_peak, peak_src = peaks()
+    g = presets.geometry(GEOM)
+    P16 = ops.DasPlan(g, rf_dtype=torch.float16)
+    rf = make_rf(P16, torch, BATCH, seed_base=1 + 1000 * rank)
+    img = torch.empty(P16.img_shape(BATCH), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    npx = g["nx"] * g["nz"]
+
+    def step():
+        P16.forward(rf, out=img)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = time_steps(torch, step, args.steps, args.warmup, stream)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    value = BATCH * npx * world / (ms * 1e-3) / 1e6
+
+    # ---- roofline of das_forward_kernel (the only launch of a step)
+    updates = active_updates(g) * BATCH
+    flops = updates * 10.0  # cubic: 4 tap MACs + 1 apodization MAC per update
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s at the maximum SM clock
+    alg_bytes = rf.numel() * 2 + img.numel() * 4
+    roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
+            "unit": "TFLOP/s", "traffic": None,
+            "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x 2070 MHz" % sms,
+            "work": "%.4g updates x 10 flop (cubic taps + apodization)" % updates}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    hbm = {"achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+           "peak_source": peak_src, "bytes_per_launch": alg_bytes}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
+
+    # ---- accuracy of this batch vs the FP64 oracle (same channel data)
+    extra = {}
+    if rank == 0:
+        import oracle
+        O = oracle.Oracle(g)
+        rng = np.random.default_rng(1)
+        errs = []
+        for f in (0, BATCH - 1):
+            pix = rng.choice(npx, 400, replace=False)
+            ref = O.das_pixels(rf[f].float().cpu().numpy().astype(np.float64), pix)
+            got = img[f].flatten()[torch.from_numpy(pix).cuda()].double().cpu().numpy()
+            errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        extra["nrmse_vs_oracle"] = float(max(errs))
+
+    # ---- other DAS cases (not the headline)
+    sub = {}
+    for nf, dt in ((1, torch.float16), (8, torch.float16), (1, torch.float32), (8, torch.float32)):
+        P = P16 if dt == torch.float16 else ops.DasPlan(g, rf_dtype=torch.float32)
+        x = rf[:nf].float().contiguous() if dt == torch.float32 else rf[:nf].contiguous()
+        y = torch.empty(P.img_shape(nf), device="cuda")
+        m = time_steps(torch, lambda: P.forward(x, out=y), max(3, args.steps), 2, stream)
+        sub["B%d_%s" % (nf, "f16" if dt == torch.float16 else "f32")] = {
+            "ms": m, "mpix_s": nf * npx / (m * 1e-3) / 1e6}
+    extra["das_cases"] = sub
+
+    # ---- tiDAS variants on the 256-frame reflectivity batch
+    if not args.no_tidas:
+        extra["tidas"] = bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak,
+                                     bf16_peak, ms / BATCH)
+
+    # ---- end to end through the public API with host buffers
+    rf_host = torch.empty(rf.shape, dtype=rf.dtype, pin_memory=True)
+    rf_host.copy_(rf)
+    img_host = torch.empty(img.shape, dtype=torch.float32, pin_memory=True)
+    rf_dev = torch.empty_like(rf)
+
+    def e2e_step():
+        rf_dev.copy_(rf_host, non_blocking=True)
+        P16.forward(rf_dev, out=img)
+        img_host.copy_(img, non_blocking=True)
+
+    e2e_ms = time_steps(torch, e2e_step, max(3, args.steps // 2), 2, stream)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": BATCH * npx * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mpixels/s",
+           "h2d_bytes_per_step": rf.numel() * 2, "d2h_bytes_per_step": img.numel() * 4}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, thr = oracle_das_sample(g, rf[0].cpu().numpy())
+        cpu = {"value": v, "unit": "Mpixels/s", "cores": thr, "kind": "oracle",
+               "sample": "%d random pixels of frame 0 (FP64 oracle DAS, 11 angles x 128 "
+                         "elements, cubic)" % n}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic",
+        "config": {"workload": "compounded plane-wave DAS: 128 el, 11 angles -10..10 deg, "
+                               "4096 samples, 512x1024 px, cubic, F#1.5, FP16 channel data, "
+                               "FP32 accumulate",
+                   "global_batch": BATCH * world, "frames_per_gpu": BATCH,
+                   "parallelism": "frames sharded across ranks, no collective",
+                   "l2": "inputs larger than L2 (738 MB per step)"},
+        "roofline": roof, "hbm": hbm, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": args.steps, "cpu_baseline": cpu,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak, bf16_peak,
+                das_ms_per_frame):
+    from paper_2507_15464_gb300.ops import DasPlan
+    P32 = DasPlan(g, rf_dtype=torch.float32)
+    kern, _ = P32.fit_kernels(TAPS)
+    nz, nx = g["nz"], g["nx"]
+    refl = torch.empty((TIDAS_FRAMES, nz, nx), dtype=torch.float32, device="cuda")
+    for f in range(TIDAS_FRAMES):
+        refl[f] = torch.from_numpy(generators.bernoulli_normal((nz, nx), 0.02, (2, f))).cuda()
+    refl_bf = refl.to(torch.bfloat16)
+    out = torch.empty_like(refl)
+    npx = TIDAS_FRAMES * nz * nx
+    res = {"frames": TIDAS_FRAMES, "taps": TAPS}
+    for variant, x, name in ((capi.VARIANT_DIRECT, refl, "direct_f32"),
+                             (capi.VARIANT_GEMM_BF16, refl_bf, "gemm_bf16"),
+                             (capi.VARIANT_GEMM_RESID, refl, "gemm_bf16_resid")):
+        try:
+            ops.tidas_forward(kern, x, variant=variant, out=out)
+        except capi.TidasError as e:
+            res[name] = {"unavailable": str(e)}
+            continue
+        m = time_steps(torch, lambda: ops.tidas_forward(kern, x, variant=variant, out=out),
+                       max(3, args.steps), 2, stream)
+        in_bytes = x.numel() * x.element_size()
+        gbs = (in_bytes + out.numel() * 4) / (m * 1e-3) / 1e9
+        r = {"ms": m, "mpix_s": npx / (m * 1e-3) / 1e6,
+             "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak},
+             "speedup_vs_das_per_frame": das_ms_per_frame / (m / TIDAS_FRAMES)}
+        # accuracy vs the FP64 oracle on sampled rows (same input values)
+        import oracle
+        rows = np.array([0, 333, 1023])
+        frames = np.array([0, TIDAS_FRAMES - 1])
+        xin = x[frames][:, rows].double().cpu().numpy()
+        ref = oracle.tidas_conv(kern[rows].cpu().numpy(), xin)
+        got = out[frames][:, rows].double().cpu().numpy()
+        r["nrmse_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        res[name] = r
+    # tiDAS vs exact DAS on the same reflectivity (first frame): DAS of the
+    # channel data that the reflectivity map produces
+    rf = P32.synthesize_grid(refl[:1].contiguous())
+    das_img = P32.forward(rf)
+    ops.tidas_forward(kern, refl[:1].contiguous(), variant=capi.VARIANT_DIRECT, out=out[:1])
+    d = das_img[0].double()
+    res["nrmse_vs_exact_das"] = float((out[0].double() - d).norm() / d.norm())
+    return res
+
+
+# ------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from tidas_workloads import presets, generators
+    g = presets.geometry(GEOM)
+    O = oracle.Oracle(g)
+    # a bounded sample of the workload: channel data of frame 0's brightest
+    # scatterers (the oracle cannot synthesise 100k scatterers per step in
+    # seconds), then FP64 DAS of a fixed set of random pixels per step
+    pos, amp = generators.compound_speckle_frame(0)
+    rf = O.synthesize(pos[-200:], amp[-200:])
+    rng = np.random.default_rng(0)
+    npx = 32768
+    pix = rng.choice(g["nx"] * g["nz"], npx, replace=False)
+    for _ in range(args.warmup):
+        O.das_pixels(rf, pix[:32])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.das_pixels(rf, pix)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = npx / dt / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixels/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "compounded plane-wave DAS: 128 el, 11 angles -10..10 deg, "
+                               "4096 samples, 512x1024 px, cubic, F#1.5 (FP64 CPU oracle)",
+                   "global_batch": 1, "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d random pixels of one frame per step" % npx},
+        "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

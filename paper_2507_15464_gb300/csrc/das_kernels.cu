@@ -63,6 +63,49 @@ __global__ void __launch_bounds__(256, 2) das_forward_kernel(DasDev d, const RF*
             const float phi = uf - fl;
             const int i = s_bi[a][tid] + (int)fl;
             const RF* row = rf + ((size_t)(f0 * A + a) * NE + n) * S;
+            const int nfb = FB > 1 ? min(FB, nf - f0) : 1;
+            if (!CHECK) {
+                // every tap inside the record: one pointer, stepped frame by frame
+                if (INTERP == TIDAS_INTERP_CUBIC) {
+                    float w0, w1, w2, w3;
+                    keys_weights(phi, w0, w1, w2, w3);
+                    const RF* p = row + (i - 1);
+                    if (nfb == FB) {
+#pragma unroll
+                        for (int f = 0; f < FB; ++f) {
+                            float v = w0 * load_rf(p);
+                            v = fmaf(w1, load_rf(p + 1), v);
+                            v = fmaf(w2, load_rf(p + 2), v);
+                            v = fmaf(w3, load_rf(p + 3), v);
+                            acc[f] = fmaf(w, v, acc[f]);
+                            p += fstride;
+                        }
+                    } else {
+#pragma unroll
+                        for (int f = 0; f < FB; ++f) {
+                            if (f >= nfb) break;
+                            float v = w0 * load_rf(p);
+                            v = fmaf(w1, load_rf(p + 1), v);
+                            v = fmaf(w2, load_rf(p + 2), v);
+                            v = fmaf(w3, load_rf(p + 3), v);
+                            acc[f] = fmaf(w, v, acc[f]);
+                            p += fstride;
+                        }
+                    }
+                } else {
+                    const float w0 = 1.f - phi, w1 = phi;
+                    const RF* p = row + i;
+#pragma unroll
+                    for (int f = 0; f < FB; ++f) {
+                        if (f >= nfb) break;
+                        float v = w0 * load_rf(p);
+                        v = fmaf(w1, load_rf(p + 1), v);
+                        acc[f] = fmaf(w, v, acc[f]);
+                        p += fstride;
+                    }
+                }
+                continue;
+            }
             if (INTERP == TIDAS_INTERP_CUBIC) {
                 float w0, w1, w2, w3;
                 keys_weights(phi, w0, w1, w2, w3);
@@ -112,10 +155,11 @@ template <typename RF, int INTERP, bool CHECK>
 static void das_forward_dispatch_fb(const DasDev& d, const void* rf, float* img, int nf,
                                     cudaStream_t st) {
     dim3 block(32, 8);
-    int fb = nf >= 8 ? 8 : (nf >= 4 ? 4 : (nf >= 2 ? 2 : 1));
+    int fb = nf >= 16 ? 16 : (nf >= 8 ? 8 : (nf >= 4 ? 4 : (nf >= 2 ? 2 : 1)));
     dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, (nf + fb - 1) / fb);
     const RF* r = (const RF*)rf;
     switch (fb) {
+        case 16: das_forward_kernel<RF, INTERP, 16, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
         case 8: das_forward_kernel<RF, INTERP, 8, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
         case 4: das_forward_kernel<RF, INTERP, 4, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
         case 2: das_forward_kernel<RF, INTERP, 2, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;

@@ -1,0 +1,56 @@
+"""Run one kernel case a few times on synthetic inputs, for profilers.
+
+python -m paper_2507_15464_gb300.profile_case das --frames 8 --dtype f16 --iters 3
+python -m paper_2507_15464_gb300.profile_case tidas --variant 1 --frames 64 --iters 3
+
+Inputs are seeded random arrays of the benchmark's shapes (the kernels'
+cost does not depend on the values); nothing is checked here.
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["das", "das_adjoint", "tidas", "tidas_adjoint"])
+    ap.add_argument("--frames", type=int, default=8)
+    ap.add_argument("--dtype", default="f16", choices=["f16", "f32"])
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--geom", default="pw128_compound")
+    a = ap.parse_args()
+
+    import torch
+    from paper_2507_15464_gb300 import ops
+    from tidas_workloads import presets
+    g = presets.geometry(a.geom)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    if a.case in ("das", "das_adjoint"):
+        dt = torch.float16 if (a.dtype == "f16" and a.case == "das") else torch.float32
+        P = ops.DasPlan(g, rf_dtype=dt)
+        if a.case == "das":
+            x = torch.randn(P.rf_shape(a.frames), device="cuda", generator=gen).to(dt)
+            fn = lambda: P.forward(x)
+        else:
+            x = torch.randn(P.img_shape(a.frames), device="cuda", generator=gen)
+            fn = lambda: P.adjoint(x)
+    else:
+        nz, nx = g["nz"], g["nx"]
+        k = torch.randn((nz, 63), device="cuda", generator=gen)
+        x = torch.randn((a.frames, nz, nx), device="cuda", generator=gen)
+        if a.variant == 1:
+            x = x.to(torch.bfloat16)
+        f = ops.tidas_forward if a.case == "tidas" else ops.tidas_adjoint
+        fn = lambda: f(k, x, variant=a.variant)
+    for _ in range(a.iters):
+        fn()
+    torch.cuda.synchronize()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main()
