@@ -170,6 +170,30 @@ int tidas_forward(const float* kernels, int32_t taps, int32_t nz, int32_t nx, co
 int tidas_adjoint(const float* kernels, int32_t taps, int32_t nz, int32_t nx, const void* img,
                   float* refl, int32_t n_frames, int32_t variant, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Deconvolution on the convolutional model (the use the paper names for it in
+ * its abstract, introduction and conclusion): min_x 1/2 ||H x - b||^2 +
+ * lambda ||x||_1 by FISTA, with H the exact DAS operator (das_forward after
+ * das_synthesize_grid) or tiDAS (tidas_forward).  Vector kernels of the
+ * iteration; n counts float32 elements. */
+
+/* *out (DEVICE double) = sum_i a[i] * b[i], accumulated in FP64.  Per-block
+ * partial sums live in a stream-ordered scratch allocation (cudaMallocAsync /
+ * cudaFreeAsync on `stream`); the final sum runs in a fixed order. */
+int tidas_dot(const float* a, const float* b, int64_t n, double* out, void* stream);
+
+/* *out (DEVICE double) = sum_i |a[i]|, FP64; scratch as tidas_dot. */
+int tidas_asum(const float* a, int64_t n, double* out, void* stream);
+
+/* One FISTA update, in place: z = y - step * grad; x' = sign(z) max(|z| - thresh, 0);
+ * y = x' + beta (x' - x); x = x'.  step > 0, thresh >= 0. */
+int tidas_fista_update(float* x, float* y, const float* grad, int64_t n, float step, float thresh,
+                       float beta, void* stream);
+
+/* out = alpha a + beta b (element-wise; out may alias a or b). */
+int tidas_axpby(const float* a, const float* b, float* out, int64_t n, float alpha, float beta,
+                void* stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* tidas_last_error(void);
 

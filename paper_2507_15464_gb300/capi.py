@@ -49,6 +49,11 @@ _SIG = {
     "tidas_forward": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_adjoint": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_device_status": [ctypes.POINTER(ctypes.c_int32)],
+    "tidas_dot": [_P, _P, ctypes.c_int64, _P, _P],
+    "tidas_asum": [_P, ctypes.c_int64, _P, _P],
+    "tidas_fista_update": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, _P],
+    "tidas_axpby": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P],
 }
 EXPORTED = list(_SIG) + ["tidas_last_error"]
 
@@ -131,6 +136,22 @@ def tidas_forward(kernels, taps, nz, nx, refl, img, n_frames, variant, stream=0)
 
 def tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream=0):
     return _check(load().tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream))
+
+
+def tidas_dot(a, b, n, out, stream=0):
+    return _check(load().tidas_dot(a, b, n, out, stream))
+
+
+def tidas_asum(a, n, out, stream=0):
+    return _check(load().tidas_asum(a, n, out, stream))
+
+
+def tidas_fista_update(x, y, grad, n, step, thresh, beta, stream=0):
+    return _check(load().tidas_fista_update(x, y, grad, n, step, thresh, beta, stream))
+
+
+def tidas_axpby(a, b, out, n, alpha, beta, stream=0):
+    return _check(load().tidas_axpby(a, b, out, n, alpha, beta, stream))
 
 
 def tidas_device_status():

@@ -1,15 +1,453 @@
-// tiDAS as per-row Toeplitz GEMMs on tcgen05 tensor cores (placeholder until
-// the tensor-core path lands).
+// tiDAS (Eq. (2.13)) as per-row Toeplitz GEMMs on the tcgen05 tensor cores.
+//
+// For one image row z the lateral convolution of every frame is
+//     Y[f, x] = sum_j R[f, j] * T_z[j, x],   T_z[j, x] = h_z[x - j + c],
+// a dense contraction over the band |x - j| <= 32 of a Toeplitz matrix.
+// Work item = (row z, 128 frames, 2 output tiles of 128 columns): UMMA
+// M = 128 frames, N = 128 columns, K = the input columns the tiles read,
+// [128 s - 32, 128 s + 160) for tile s, in chunks of 64 columns (the
+// 128-byte swizzle width of BF16).  T_z restricted to (chunk offset c',
+// tile) does not depend on the tile (shift invariance): three 128 x 64
+// operand tiles per row, built in shared memory from the row's taps, serve
+// every tile of the row.
+//
+// Persistent, warp-specialised kernel; each CTA walks a contiguous range of
+// items (consecutive items share a row):
+//   warp 0      TMA producer of BF16 input chunks (zero fill outside the row)
+//   warp 1      tensor-memory owner; lane 0 issues the MMAs
+//   warps 2-5   epilogue: tensor memory -> registers -> swizzled shared tile
+//               -> TMA tensor store (whole 128-byte lines)
+//   warps 6-7   build the next row's Toeplitz tiles (double buffered)
+//   warps 8-11  (residual variant) load FP32 input and split it into BF16
+//               hi / lo operand tiles
+// Accumulators are double buffered in tensor memory so the epilogue of one
+// item overlaps the MMAs of the next.  The residual variant adds the two
+// first-order low-part products of r = r_hi + r_lo, h = h_hi + h_lo (r_lo,
+// h_lo the BF16 roundings of the remainders) into the same accumulators.
 #include "common.cuh"
+#include "sm103_primitives.cuh"
 
 namespace tidas {
 // Written by bounded waits of the tensor-core kernels; read by tidas_device_status.
 __device__ int g_wait_error = 0;
 
-int launch_tidas_gemm(const float*, int, int, bool, int, int, const void*, float*, int, bool,
-                      cudaStream_t) {
-    return set_error(TIDAS_ERR_UNSUPPORTED, "tidas GEMM variants not built yet");
+using namespace sm103;
+
+namespace gemm {
+constexpr int kM = 128;                    // frames per item (UMMA M)
+constexpr int kN = 128;                    // outputs per tile (UMMA N)
+constexpr int kKC = 64;                    // input columns per K-chunk
+constexpr int kTilesPerItem = 2;
+constexpr int kChunkBytes = kM * kKC * 2;  // 16 KB of BF16
+constexpr int kBTileBytes = kN * kKC * 2;  // 16 KB
+constexpr int kOutTileBytes = 32 * 32 * 4; // 32 frames x 32 columns of FP32
+constexpr uint32_t kAccCols = kTilesPerItem * kN;  // 256 columns per accumulator buffer
+constexpr uint32_t kTmemCols = 2 * kAccCols;       // double buffered
+constexpr uint32_t kIdesc = idesc_bf16_f32(kM, kN);
+constexpr int kWaitEmpty = 101, kWaitFull = 102, kWaitAcc = 103, kWaitDrain = 104, kWaitConv = 105,
+              kWaitB = 106, kWaitAccFree = 107;
+
+template <bool RESID>
+struct Cfg {
+    static constexpr int kStages = RESID ? 2 : 4;   // operand ring (BF16 hi[/lo] tiles)
+    static constexpr int kBBufs = RESID ? 1 : 2;
+    static constexpr int kBParts = RESID ? 2 : 1;   // hi [, lo]
+    static constexpr int kAParts = RESID ? 2 : 1;
+    static constexpr int kWarps = RESID ? 12 : 8;
+    static constexpr int kThreads = kWarps * 32;
+    static constexpr size_t kOffA = 0;
+    static constexpr size_t kOffB = kOffA + (size_t)kStages * kAParts * kChunkBytes;
+    static constexpr size_t kOffO = kOffB + (size_t)kBBufs * kBParts * 3 * kBTileBytes;
+    static constexpr size_t kOffBar = kOffO + (size_t)4 * 2 * kOutTileBytes;
+    static constexpr size_t kSmem = 1024 + kOffBar + 1024;  // barriers, TMEM slot, taps
+};
+
+struct Item {
+    int z, m0, s0, s1;
+};
+__device__ __forceinline__ Item decode(int it, int nh, int nm, int ntiles) {
+    Item r;
+    const int h = it % nh;
+    r.m0 = ((it / nh) % nm) * kM;
+    r.z = it / (nh * nm);
+    r.s0 = h * kTilesPerItem;
+    r.s1 = min(ntiles, r.s0 + kTilesPerItem);
+    return r;
 }
+}  // namespace gemm
+
+template <bool RESID>
+__global__ void __launch_bounds__(gemm::Cfg<RESID>::kThreads, 1)
+    tidas_gemm_kernel(const __grid_constant__ CUtensorMap tmap_in,
+                      const __grid_constant__ CUtensorMap tmap_out, const float* __restrict__ in32,
+                      const float* __restrict__ kern, int taps, int center, int adjoint, int nz,
+                      int nx, int nf) {
+    using namespace gemm;
+    using C = Cfg<RESID>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base + C::kOffA;  // [stage][part] BF16 tiles
+    uint8_t* sB = base + C::kOffB;  // [buf][part][3] Toeplitz tiles
+    uint8_t* sO = base + C::kOffO;  // [epilogue warp][2] output staging tiles
+    uint64_t* full = (uint64_t*)(base + C::kOffBar);
+    uint64_t* empty = full + C::kStages;
+    uint64_t* b_full = empty + C::kStages;
+    uint64_t* b_empty = b_full + 2;
+    uint64_t* acc_full = b_empty + 2;
+    uint64_t* acc_empty = acc_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+    volatile int* s_abort = (volatile int*)(tmem_slot + 1);
+    float* s_taps = (float*)(tmem_slot + 4);  // [kBBufs][64]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (nx + kN - 1) / kN;
+    const int nh = (ntiles + kTilesPerItem - 1) / kTilesPerItem;
+    const int nm = (nf + kM - 1) / kM;
+    const int total = nz * nm * nh;
+    const int it_begin = (int)((long long)blockIdx.x * total / gridDim.x);
+    const int it_end = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mbar_init(&full[s], RESID ? 4 : 1);  // TMA (tx) or the four converter warps
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&b_full[s], 2);
+            mbar_init(&b_empty[s], 1);
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+        }
+        *s_abort = 0;
+        fence_barrier_init();
+        if (!RESID) prefetch_tensormap(&tmap_in);
+        prefetch_tensormap(&tmap_out);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (!RESID && lane == 0) {
+            uint32_t st = 0, ph = 0;
+            int issued = 0;
+            for (int it = it_begin; it < it_end && !*s_abort; ++it) {
+                const Item I = decode(it, nh, nm, ntiles);
+                for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                    if (!mbar_wait(&empty[st], ph ^ 1, &g_wait_error, kWaitEmpty)) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], kChunkBytes);
+                    tma_load_3d(sA + st * kChunkBytes, &tmap_in, &full[st], kKC * c - 32, I.z,
+                                I.m0);
+                    if (++st == (uint32_t)C::kStages) { st = 0; ph ^= 1; }
+                    ++issued;
+                }
+            }
+            if (*s_abort) {
+                // let issued copies land before shared memory is released
+                for (int q = 0; q < min(issued, C::kStages); ++q) {
+                    st = (st == 0) ? C::kStages - 1 : st - 1;
+                    if (st == (uint32_t)C::kStages - 1) ph ^= 1;
+                    mbar_wait(&full[st], ph, &g_wait_error, kWaitDrain);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // --------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            int prev_z = -1, nrow = -1, k = 0;
+            for (int it = it_begin; it < it_end && !*s_abort; ++it, ++k) {
+                const Item I = decode(it, nh, nm, ntiles);
+                if (I.z != prev_z) {
+                    if (nrow >= 0) mma_commit(&b_empty[nrow % C::kBBufs]);
+                    ++nrow;
+                    prev_z = I.z;
+                    if (!mbar_wait(&b_full[nrow % C::kBBufs], (nrow / C::kBBufs) & 1,
+                                   &g_wait_error, kWaitB)) {
+                        *s_abort = 1;
+                        break;
+                    }
+                }
+                const int ab = k & 1;
+                if (!mbar_wait(&acc_empty[ab], ((k >> 1) & 1) ^ 1, &g_wait_error, kWaitAccFree)) {
+                    *s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint8_t* bt = sB + (size_t)(nrow % C::kBBufs) * C::kBParts * 3 * kBTileBytes;
+                for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                    if (!mbar_wait(&full[st], ph, &g_wait_error, kWaitFull)) {
+                        *s_abort = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem_u32(sA + st * C::kAParts * kChunkBytes);
+                    const uint32_t a_lo = a_hi + kChunkBytes;
+                    int tl[2], cp[2], np = 0;
+                    if ((c & 1) == 0 && c / 2 - 1 >= I.s0) { tl[np] = c / 2 - 1; cp[np] = 2; ++np; }
+                    if (c / 2 < I.s1) { tl[np] = c / 2; cp[np] = c & 1; ++np; }
+                    for (int q = 0; q < np; ++q) {
+                        const uint32_t d = tmem_base + (uint32_t)(ab * kAccCols) +
+                                           (uint32_t)((tl[q] - I.s0) * kN);
+                        const uint32_t bh = smem_u32(bt + cp[q] * kBTileBytes);
+                        const uint32_t bl = bh + 3 * kBTileBytes;
+#pragma unroll
+                        for (int kk = 0; kk < kKC / 16; ++kk) {
+                            const uint32_t acc = (cp[q] > 0 || kk > 0) ? 1u : 0u;
+                            mma_f16(d, desc_sw128_kmajor(a_hi) + 2 * kk,
+                                    desc_sw128_kmajor(bh) + 2 * kk, kIdesc, acc);
+                            if (RESID) {
+                                mma_f16(d, desc_sw128_kmajor(a_lo) + 2 * kk,
+                                        desc_sw128_kmajor(bh) + 2 * kk, kIdesc, 1u);
+                                mma_f16(d, desc_sw128_kmajor(a_hi) + 2 * kk,
+                                        desc_sw128_kmajor(bl) + 2 * kk, kIdesc, 1u);
+                            }
+                        }
+                    }
+                    mma_commit(&empty[st]);
+                    if (++st == (uint32_t)C::kStages) { st = 0; ph ^= 1; }
+                }
+                mma_commit(&acc_full[ab]);
+            }
+            if (nrow >= 0) mma_commit(&b_empty[nrow % C::kBBufs]);
+        }
+        __syncwarp();
+    } else if (warp < 6) {
+        // ------------------------------------------------------ epilogue
+        const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+        uint8_t* stage_buf = sO + (size_t)(warp - 2) * 2 * kOutTileBytes;
+        int k = 0, q = 0;
+        for (int it = it_begin; it < it_end && !*s_abort; ++it, ++k) {
+            const Item I = decode(it, nh, nm, ntiles);
+            const int ab = k & 1;
+            if (!mbar_wait(&acc_full[ab], (k >> 1) & 1, &g_wait_error, kWaitAcc)) {
+                *s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            for (int s = I.s0; s < I.s1; ++s) {
+#pragma unroll 1
+                for (int j = 0; j < kN / 32; ++j, ++q) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                           (uint32_t)(ab * kAccCols + (s - I.s0) * kN + j * 32),
+                                       r);
+                    tmem_ld_wait();
+                    uint8_t* tile = stage_buf + (q & 1) * kOutTileBytes;
+                    // the store issued two tiles ago must have finished reading `tile`
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+                    // row `lane` of the 32 x 32 tile, 16-byte chunks XOR-swizzled by row
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; ++c4)
+                        *reinterpret_cast<uint4*>(tile + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                            make_uint4(r[4 * c4], r[4 * c4 + 1], r[4 * c4 + 2], r[4 * c4 + 3]);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_3d(&tmap_out, tile, s * kN + j * 32, I.z, I.m0 + quarter * 32);
+                        bulk_commit();
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+        if (lane == 0) bulk_wait<0>();
+        __syncwarp();
+    } else if (warp < 8) {
+        // --------------------------------------- Toeplitz operand builders
+        const int bt = threadIdx.x - 6 * 32;  // 0..63
+        int prev_z = -1, nrow = -1;
+        for (int it = it_begin; it < it_end && !*s_abort; ++it) {
+            const Item I = decode(it, nh, nm, ntiles);
+            if (I.z == prev_z) continue;
+            prev_z = I.z;
+            ++nrow;
+            const int b = nrow % C::kBBufs;
+            if (!mbar_wait(&b_empty[b], ((nrow / C::kBBufs) & 1) ^ 1, &g_wait_error, kWaitB)) {
+                *s_abort = 1;
+                break;
+            }
+            float* tp = s_taps + b * 64;
+            if (bt < 64) tp[bt] = bt < taps ? __ldg(kern + (size_t)I.z * taps + bt) : 0.f;
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            uint8_t* dst = sB + (size_t)b * C::kBParts * 3 * kBTileBytes;
+            for (int idx = bt; idx < 3 * kN * kKC / 2; idx += 64) {
+                // two consecutive k per thread
+                const int c = idx / (kN * kKC / 2), rem = idx % (kN * kKC / 2);
+                const int n = rem / (kKC / 2), k2 = (rem % (kKC / 2)) * 2;
+                float v[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int kk = k2 + e;
+                    const int t = adjoint ? (kk + kKC * c - n - 32 + center)
+                                          : (n - kk - kKC * c + 32 + center);
+                    v[e] = (t >= 0 && t < taps) ? tp[t] : 0.f;
+                }
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(v[0], v[1]);
+                const uint32_t off = c * kBTileBytes + sw128_offset(n, k2);
+                *reinterpret_cast<__nv_bfloat162*>(dst + off) = hi;
+                if (RESID) {
+                    const float2 hf = __bfloat1622float2(hi);
+                    *reinterpret_cast<__nv_bfloat162*>(dst + 3 * kBTileBytes + off) =
+                        __floats2bfloat162_rn(v[0] - hf.x, v[1] - hf.y);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&b_full[b]);
+        }
+    } else if (RESID) {
+        // ------------------------- FP32 input -> BF16 hi / lo operand tiles
+        const int ct = threadIdx.x - 8 * 32;  // 0..127
+        uint32_t ast = 0, aph = 0;
+        for (int it = it_begin; it < it_end && !*s_abort; ++it) {
+            const Item I = decode(it, nh, nm, ntiles);
+            for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                if (*s_abort || !mbar_wait(&empty[ast], aph ^ 1, &g_wait_error, kWaitConv)) {
+                    *s_abort = 1;
+                    break;
+                }
+                uint8_t* dhi = sA + ast * 2 * kChunkBytes;
+                uint8_t* dlo = dhi + kChunkBytes;
+                const int xb = kKC * c - 32;
+                float4 v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int id = ct + 128 * i;
+                    const int row = id >> 4, x = xb + (id & 15) * 4;
+                    const int f = I.m0 + row;
+                    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (f < nf && x >= 0 && x < nx)
+                        v[i] = __ldcs(reinterpret_cast<const float4*>(
+                            in32 + ((size_t)f * nz + I.z) * nx + x));
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int id = ct + 128 * i;
+                    const int row = id >> 4, kq = (id & 15) * 4;
+                    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[i].x, v[i].y);
+                    const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[i].z, v[i].w);
+                    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[i].x - f01.x, v[i].y - f01.y);
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[i].z - f23.x, v[i].w - f23.y);
+                    const uint32_t off = sw128_offset(row, kq);
+                    uint2 ph2, pl2;
+                    ph2.x = *reinterpret_cast<const uint32_t*>(&h01);
+                    ph2.y = *reinterpret_cast<const uint32_t*>(&h23);
+                    pl2.x = *reinterpret_cast<const uint32_t*>(&l01);
+                    pl2.y = *reinterpret_cast<const uint32_t*>(&l23);
+                    *reinterpret_cast<uint2*>(dhi + off) = ph2;
+                    *reinterpret_cast<uint2*>(dlo + off) = pl2;
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[ast]);
+                if (++ast == (uint32_t)C::kStages) { ast = 0; aph ^= 1; }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// ------------------------------------------------------------------ host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 3D map over a [nf][nz][nx] array; box = box_x columns x 1 row x box_f frames
+int make_map_3d(CUtensorMap* map, const void* ptr, CUtensorMapDataType dt, int esize, int nz,
+                int nx, int nf, int box_x, int box_f, CUtensorMapSwizzle sw) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)nz, (cuuint64_t)nf};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * nz * esize};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, 1u, (cuuint32_t)box_f};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = enc(map, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TIDAS_OK;
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int nz, int nx,
+                      const void* in, float* out, int nf, bool resid, cudaStream_t st) {
+    CUtensorMap map_in, map_out;
+    // output: 32 columns x 1 row x 32 frames of FP32, 128-byte swizzled staging
+    int rc = make_map_3d(&map_out, out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nz, nx, nf, 32, 32,
+                         CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    if (resid) {
+        map_in = map_out;  // unused by the residual kernel (it reads FP32 directly)
+    } else {
+        rc = make_map_3d(&map_in, in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nz, nx, nf, gemm::kKC,
+                         gemm::kM, CU_TENSOR_MAP_SWIZZLE_128B);
+        if (rc) return rc;
+    }
+    const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
+    const int items = nz * ((nf + gemm::kM - 1) / gemm::kM) *
+                      ((ntiles + gemm::kTilesPerItem - 1) / gemm::kTilesPerItem);
+    const int grid = items < sm_count() ? items : sm_count();
+    if (resid) {
+        using C = gemm::Cfg<true>;
+        cudaFuncSetAttribute(tidas_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::kSmem);
+        tidas_gemm_kernel<true><<<grid, C::kThreads, C::kSmem, st>>>(
+            map_in, map_out, (const float*)in, kern, taps, center, adjoint ? 1 : 0, nz, nx, nf);
+    } else {
+        using C = gemm::Cfg<false>;
+        cudaFuncSetAttribute(tidas_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::kSmem);
+        tidas_gemm_kernel<false><<<grid, C::kThreads, C::kSmem, st>>>(
+            map_in, map_out, nullptr, kern, taps, center, adjoint ? 1 : 0, nz, nx, nf);
+    }
+    return check_launch("tidas_gemm_kernel");
+}
+
 }  // namespace tidas
 
 extern "C" int tidas_device_status(int32_t* status) {

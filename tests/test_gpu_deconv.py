@@ -1,0 +1,170 @@
+"""GPU parity of the deconvolution layer: FP64 reductions, the fused FISTA
+update, autograd backward passes (= adjoint kernels) against central finite
+differences, and whole FISTA runs against the FP64 oracle FISTA.
+
+Tolerances: reductions 1e-12 relative (FP64 sums of the same FP32 values);
+finite-difference gradients 2e-3 relative (step 1e-3 in FP32); FISTA iterates
+after k steps against the FP64 oracle 1e-4 (tiDAS) and 1e-3 (exact operator),
+the FP32 operator error ~1e-6 per application grown over the iterations.
+"""
+import numpy as np
+import pytest
+
+from tidas_workloads import generators, presets
+
+from .gpu_helpers import dot_test, host, rel_l2, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def D():
+    from paper_2507_15464_gb300 import deconv
+    return deconv
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 10_000_003])
+def test_fp64_reductions(n):
+    a = generators.standard_normal((n,), (40,))
+    b = generators.standard_normal((n,), (41,))
+    ta, tb = to_dev(a), to_dev(b)
+    d = float(D().dot(ta, tb))
+    s = float(D().asum(ta))
+    ref_d = float(np.dot(a.astype(np.float64), b.astype(np.float64)))
+    ref_s = float(np.abs(a.astype(np.float64)).sum())
+    assert abs(d - ref_d) <= 1e-12 * max(1.0, np.linalg.norm(a) * np.linalg.norm(b))
+    assert abs(s - ref_s) <= 1e-12 * max(1.0, ref_s)
+
+
+def test_fista_update_kernel():
+    from paper_2507_15464_gb300 import capi
+    from paper_2507_15464_gb300.ops import _ptr
+    from oracle import fista as F
+    n = 100_001
+    x = generators.standard_normal((n,), (42,))
+    y = generators.standard_normal((n,), (43,))
+    g = generators.standard_normal((n,), (44,))
+    tx, ty, tg = to_dev(x), to_dev(y), to_dev(g)
+    step, thresh, beta = 0.37, 0.21, 0.6
+    capi.tidas_fista_update(_ptr(tx), _ptr(ty), _ptr(tg), n, step, thresh, beta)
+    xn = F.soft(y.astype(np.float64) - step * g, thresh)
+    yn = xn + beta * (xn - x)
+    np.testing.assert_allclose(host(tx), xn, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(host(ty), yn, rtol=1e-5, atol=1e-5)
+
+
+def _tidas_problem(nz=64, nx=128, taps=31, seed=45):
+    kern = generators.standard_normal((nz, taps), (seed,))
+    x_true = generators.bernoulli_normal((1, nz, nx), 0.05, (seed, 1))
+    noise = generators.standard_normal((1, nz, nx), (seed, 2))
+    return kern, x_true, noise
+
+
+def test_fista_tidas_matches_oracle():
+    import oracle
+    from oracle import fista as F
+    from paper_2507_15464_gb300 import capi
+    deconv = D()
+    kern, x_true, noise = _tidas_problem()
+    H = lambda v: oracle.tidas_conv(kern, v)
+    Ht = lambda v: oracle.tidas_conv_adjoint(kern, v)
+    b = H(x_true) + 0.01 * noise
+    b32 = b.astype(np.float32)
+    v0 = generators.standard_normal(b.shape, (46,))
+    L, _ = F.power_iteration(H, Ht, v0, 30)
+    op = deconv.TidasOperator(to_dev(kern), capi.VARIANT_DIRECT)
+    Lg, _ = deconv.power_iteration(op, to_dev(v0), 30)
+    assert Lg == pytest.approx(L, rel=1e-5)
+    lam = 0.01 * np.abs(Ht(b32)).max()
+    x_o = F.fista(H, Ht, b32.astype(np.float64), lam, 1.01 * L, 100)
+    x_g = host(deconv.fista(op, to_dev(b32), lam, 1.01 * L, 100))
+    assert rel_l2(x_g, x_o) <= 1e-4
+    # the objective decreased from x = 0
+    assert F.objective(H, x_o, b32, lam) < F.objective(H, 0 * x_o, b32, lam)
+
+
+def test_fista_exact_operator_matches_oracle():
+    import oracle
+    from oracle import fista as F
+    from paper_2507_15464_gb300.ops import DasPlan
+    deconv = D()
+    g = presets.geometry("pw64_single", nz=24, nx=32, z0=14e-3, x0=-2.4e-3, n_samples=1400)
+    O = oracle.Oracle(g)
+    P = DasPlan(g)
+    H = lambda v: O.das(O.synth_grid(v[0]))[None]
+    Ht = lambda v: O.synth_adjoint(O.das_adjoint(v[0]))[None]
+    x_true = generators.bernoulli_normal((1, 24, 32), 0.05, (47,))
+    b = (H(x_true) + 0.01 * generators.standard_normal((1, 24, 32), (48,))).astype(np.float32)
+    L, _ = F.power_iteration(H, Ht, generators.standard_normal((1, 24, 32), (49,)), 20)
+    lam = 0.01 * np.abs(Ht(b)).max()
+    x_o = F.fista(H, Ht, b.astype(np.float64), lam, 1.01 * L, 15)
+    x_g = host(deconv.fista(deconv.ExactOperator(P), to_dev(b), lam, 1.01 * L, 15))
+    assert rel_l2(x_g, x_o) <= 1e-3
+
+
+def _fd_check(loss_fn, x, v, eps=1e-3):
+    xg = x.clone().requires_grad_(True)
+    loss = loss_fn(xg)
+    loss.backward()
+    g_dot_v = float((xg.grad.double() * v.double()).sum())
+    with torch.no_grad():
+        fd = (float(loss_fn(x + eps * v)) - float(loss_fn(x - eps * v))) / (2 * eps)
+    assert abs(g_dot_v - fd) <= 2e-3 * abs(fd), (g_dot_v, fd, eps)
+
+
+def _crop_direction(shape, seed):
+    v = np.zeros(shape, np.float32)
+    v[0, 400:464, 300:364] = generators.standard_normal((64, 64), (seed,))
+    return to_dev(v)
+
+
+def test_autograd_exact_operator_finite_differences():
+    from paper_2507_15464_gb300.ops import DasPlan
+    deconv = D()
+    g = presets.geometry("pw128_deconv")
+    P = DasPlan(g)
+    shape = (1, 1024, 1024)
+    x = np.zeros(shape, np.float32)
+    x[0, 380:480, 280:380] = generators.bernoulli_normal((100, 100), 0.2, (50,))
+    x = to_dev(x)
+    b = to_dev(generators.standard_normal(shape, (51,)) * 0.1)
+
+    def loss(z):
+        r = deconv.exact_operator(z, P) - b
+        return 0.5 * (r.double() ** 2).sum()
+
+    _fd_check(loss, x, _crop_direction(shape, 52))
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_autograd_tidas_finite_differences(variant):
+    from paper_2507_15464_gb300.ops import DasPlan
+    deconv = D()
+    g = presets.geometry("pw128_deconv")
+    kern, _ = DasPlan(g).fit_kernels(63)
+    shape = (1, 1024, 1024)
+    x = to_dev(generators.bernoulli_normal(shape, 0.02, (53,)))
+    b = to_dev(generators.standard_normal(shape, (54,)))
+
+    def loss(z):
+        r = deconv.tidas(z, kern, variant) - b
+        return 0.5 * (r.double() ** 2).sum()
+
+    _fd_check(loss, x, _crop_direction(shape, 55))
+
+
+def test_exact_operator_adjoint_identity():
+    from paper_2507_15464_gb300.ops import DasPlan
+    deconv = D()
+    g = presets.geometry("pw128_deconv", nz=256)
+    P = DasPlan(g)
+    op = deconv.ExactOperator(P)
+    x = to_dev(generators.bernoulli_normal((1, 256, 1024), 0.05, (56,)))
+    y = to_dev(generators.standard_normal((1, 256, 1024), (57,)))
+    hx = op.forward(x, None)
+    hty = op.adjoint(y, torch.empty_like(x))
+    dot_test(host(hx), host(y), host(x), host(hty))

@@ -46,7 +46,7 @@ def _run(variant, kern, refl, adjoint=False):
 
 
 def _variants():
-    return [0]
+    return [0, 1, 2]
 
 
 @pytest.mark.parametrize("variant", _variants())
