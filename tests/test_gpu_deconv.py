@@ -154,7 +154,11 @@ def test_autograd_tidas_finite_differences(variant):
         r = deconv.tidas(z, kern, variant) - b
         return 0.5 * (r.double() ** 2).sum()
 
-    _fd_check(loss, x, _crop_direction(shape, 55))
+    # Central differences are exact for this quadratic loss; what limits them
+    # is the forward's own rounding.  The residual variant splits its input
+    # into BF16 hi / lo parts, a rounding with relative jumps ~2^-16, which at
+    # step 1e-3 is ~1 % of the difference quotient: it takes step 0.1.
+    _fd_check(loss, x, _crop_direction(shape, 55), eps=1e-3 if variant == 0 else 0.1)
 
 
 def test_exact_operator_adjoint_identity():
