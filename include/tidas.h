@@ -182,6 +182,19 @@ int tidas_adjoint(const float* kernels, int32_t taps, int32_t nz, int32_t nx, co
  * cudaFreeAsync on `stream`); the final sum runs in a fixed order. */
 int tidas_dot(const float* a, const float* b, int64_t n, double* out, void* stream);
 
+/* Same result as tidas_dot, without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot let a library allocate,
+ * such as a streaming scanner pipeline that reserves its whole device budget
+ * at start-up and treats later allocations as failures, or a host thread
+ * that must not wait on an allocator.  The per-block partial sums live in a
+ * fixed 32 KB device array inside the library (held on every GPU that loads
+ * it until exit), so n is limited to 16,777,216 elements; larger n returns
+ * TIDAS_ERR_ARG before anything is enqueued.  The first call on each device
+ * looks up the array's device address (with that device current); make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU, for example on two streams, race and give wrong sums. */
+int tidas_dot_noalloc(const float* a, const float* b, int64_t n, double* out, void* stream);
+
 /* *out (DEVICE double) = sum_i |a[i]|, FP64; scratch as tidas_dot. */
 int tidas_asum(const float* a, int64_t n, double* out, void* stream);
 

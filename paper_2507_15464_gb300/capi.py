@@ -50,6 +50,7 @@ _SIG = {
     "tidas_adjoint": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_device_status": [ctypes.POINTER(ctypes.c_int32)],
     "tidas_dot": [_P, _P, ctypes.c_int64, _P, _P],
+    "tidas_dot_noalloc": [_P, _P, ctypes.c_int64, _P, _P],
     "tidas_asum": [_P, ctypes.c_int64, _P, _P],
     "tidas_fista_update": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, _P],
@@ -70,10 +71,10 @@ def load(build_if_missing=True):
     if _lib is not None:
         return _lib
     path = _build.LIB
-    if not os.path.exists(path):
-        if not build_if_missing:
-            raise OSError("libtidas.so has not been built: run __graft_entry__.build()")
-        _build.build()
+    if build_if_missing:
+        _build.build()  # no-op when the library is newer than its sources
+    elif not os.path.exists(path):
+        raise OSError("libtidas.so has not been built: run __graft_entry__.build()")
     L = ctypes.CDLL(path)
     for name, args in _SIG.items():
         f = getattr(L, name)
@@ -140,6 +141,10 @@ def tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream=0)
 
 def tidas_dot(a, b, n, out, stream=0):
     return _check(load().tidas_dot(a, b, n, out, stream))
+
+
+def tidas_dot_noalloc(a, b, n, out, stream=0):
+    return _check(load().tidas_dot_noalloc(a, b, n, out, stream))
 
 
 def tidas_asum(a, n, out, stream=0):

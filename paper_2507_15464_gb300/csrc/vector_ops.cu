@@ -133,3 +133,57 @@ extern "C" int tidas_axpby(const float* a, const float* b, float* out, int64_t n
     axpby_kernel<<<vec_blocks(n), 256, 0, (cudaStream_t)stream>>>(a, b, out, n, alpha, beta);
     return check_launch("axpby_kernel");
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 dot product.
+//
+// Some callers cannot let the library allocate device memory: a scanner or
+// streaming pipeline that reserves its whole device budget when it starts and
+// treats any later allocation as a failure, or a host thread that must not
+// wait on an allocator.  For them the per-block partial sums of tidas_dot live
+// in the fixed array below instead of a stream-ordered allocation.
+//
+// The array is a file-scope device variable: every GPU that loads the library
+// holds it until the process exits.  Host code cannot use the name of the
+// array as a device address, so the first call on each device looks the
+// address up with cudaGetSymbolAddress (with that device current) and keeps
+// it; make that first call before any stream capture.  All calls share the
+// array and it keeps the previous call's contents; every partial this call
+// reads is written by the same call first, so nothing needs clearing.  Calls
+// that overlap on the GPU (for example on two streams) race on the array.
+namespace tidas {
+constexpr int kNoAllocPartials = 4096;                       // 32 KB of FP64 partials
+constexpr long long kNoAllocPerBlock = 4096;                 // elements per partial sum
+constexpr long long kNoAllocMaxN = kNoAllocPartials * kNoAllocPerBlock;  // 16,777,216
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+}  // namespace tidas
+
+#include <mutex>
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[256] = {nullptr};
+
+extern "C" int tidas_dot_noalloc(const float* a, const float* b, int64_t n, double* out,
+                                 void* stream) {
+    TIDAS_REQUIRE(out && (n == 0 || (a && b)), "tidas_dot_noalloc: null pointer");
+    TIDAS_REQUIRE(n >= 0, "tidas_dot_noalloc: negative length");
+    TIDAS_REQUIRE(n <= kNoAllocMaxN,
+                  "tidas_dot_noalloc: n = %lld exceeds the fixed scratch limit of %lld elements",
+                  (long long)n, kNoAllocMaxN);
+    int dev = 0;
+    TIDAS_CUDA(cudaGetDevice(&dev));
+    TIDAS_REQUIRE(dev >= 0 && dev < 256, "tidas_dot_noalloc: device index %d out of range", dev);
+    double* partial;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            TIDAS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partials));
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        partial = g_noalloc_ptr[dev];
+    }
+    long long nb = (n + kNoAllocPerBlock - 1) / kNoAllocPerBlock;
+    if (nb < 1) nb = 1;
+    return launch_reduce(a, b, n, 0, partial, (int)nb, out, (cudaStream_t)stream);
+}
