@@ -207,6 +207,85 @@ int tidas_fista_update(float* x, float* y, const float* grad, int64_t n, float s
 int tidas_axpby(const float* a, const float* b, float* out, int64_t n, float alpha, float beta,
                 void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned kernel generator.  The paper's conclusion names learned scaling
+ * parameters Theta as the way forward; here a small MLP maps (x, z, F#,
+ * transmit angle) to the row kernel, trained on exact PSFs.  These are its
+ * training targets, its GEMM, and the small kernels of training and
+ * inference.  BF16 arrays are passed as void*. */
+
+/* Exact single-scatterer PSF rows (Section 2.2, Eq. (2.6)-(2.7)) for a batch
+ * of acquisitions: samples [n][4] float64 = (x, z, F#, theta_rad), a unit
+ * scatterer at (x, z), one plane wave at theta, receive f-number F#, the
+ * plan's array, pulse, interpolation and lateral spacing dx.  out[i][t]
+ * (row stride ldo >= taps, columns >= taps zeroed) = DAS value at
+ * (x + (t - taps/2) dx, z).  If norm != NULL, rows are divided by the sum of
+ * the apodization weights at (x, z), written to norm[i]. */
+int tidas_psf_batch(das_plan plan, const double* samples, int32_t n, int32_t taps, float* out,
+                    int32_t ldo, float* norm, void* stream);
+
+/* out[i] = sum of the receive apodization weights at (x, z) for F#
+ * (samples as tidas_psf_batch; the kernel scale). */
+int tidas_apod_sum(das_plan plan, const double* samples, int64_t n, float* out, void* stream);
+
+/* C[M x N] = act(A[M x K] * B[N x K]^T + bias[N]) on tcgen05 tensor cores.
+ * A, B: row-major BF16 with K contiguous; FP32 accumulation.  K % 64 == 0,
+ * N % 16 == 0, 16-byte aligned arrays.  bias: float[N] or NULL; relu != 0
+ * applies max(., 0).  Outputs (either may be NULL): c32 float, c16 BF16,
+ * row stride ldc (ldc % 8 == 0). */
+int tidas_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                    const float* bias, int32_t relu, float* c32, void* c16, int32_t ldc,
+                    void* stream);
+
+/* out[cols][rows] = in[rows][cols]^T, BF16. */
+int tidas_transpose_bf16(const void* in, int32_t rows, int32_t cols, void* out, void* stream);
+
+/* dst[i] = src[idx[i]], i < n, for rows of row_bytes (multiple of 4) bytes. */
+int tidas_gather_rows(const void* src, const int32_t* idx, int64_t n, int32_t row_bytes, void* dst,
+                      void* stream);
+
+/* ReLU backward: dpre = act > 0 ? dpost : 0 (act = post-ReLU activation, or
+ * NULL for a plain copy); dpre32 (float, may be NULL) and dpre16 (BF16) outputs. */
+int tidas_relu_backward(const float* dpost, const float* act, int64_t n, float* dpre32,
+                        void* dpre16, void* stream);
+
+/* db[j] = sum_i d[i * ld + j], i < rows, j < cols. */
+int tidas_colsum(const float* d, int32_t rows, int32_t cols, int32_t ld, float* db, void* stream);
+
+/* AdamW step `step` (>= 1) on FP32 master weights w[rows][cols] with moments
+ * m, v and gradient g; refreshes the BF16 copy w16 and its transpose w16t
+ * (either may be NULL). */
+int tidas_adam(float* w, float* m, float* v, const float* g, int32_t rows, int32_t cols, float lr,
+               float b1, float b2, float eps, float wd, int32_t step, void* w16, void* w16t,
+               void* stream);
+
+/* Mean squared error over the first cols_used columns: *loss (DEVICE double),
+ * dpred = 2 (pred - target) / (rows cols_used), zero in unused columns.
+ * Partial sums use stream-ordered scratch (cudaMallocAsync / cudaFreeAsync). */
+int tidas_mse(const float* pred, const float* target, int32_t rows, int32_t cols_used, int32_t ldp,
+              int32_t ldt, float* dpred, double* loss, void* stream);
+
+/* Network inputs: out16[i][0..63] = BF16(2 (s_ic - lo[c]) / (hi[c] - lo[c]) - 1)
+ * for the 4 features of samples [n][4], zeros in columns 4..63.  lo4 / hi4
+ * are DEVICE float[4]. */
+int tidas_encode(const double* samples, int32_t n, const float* lo4, const float* hi4, void* out16,
+                 void* stream);
+
+/* Eq. (2.13) with a kernel per pixel: img[f][z][x] = sum_t h[z][x][t] *
+ * refl[f][z][x - t + taps/2]; kernels [nz * nx][ld], taps <= 64. */
+int tidas_forward_varying(const float* kernels, int32_t ld, int32_t taps, int32_t nz, int32_t nx,
+                          const float* refl, float* img, int32_t n_frames, void* stream);
+
+/* Per-pixel NRMSE of learned vs exact kernels (nrmse[p], may be NULL); out
+ * takes the exact kernel where the NRMSE exceeds thresh, else the learned one. */
+int tidas_kernel_fallback(const float* learned, int32_t ldl, const float* exact, int32_t lde,
+                          int64_t npix, int32_t taps, float thresh, float* out, int32_t ldo,
+                          float* nrmse, void* stream);
+
+/* out[i][t] = in[i][t] * s[i] for t < cols (kernel de-normalisation). */
+int tidas_row_scale(const float* in, int32_t ldi, const float* s, int64_t rows, int32_t cols,
+                    float* out, int32_t ldo, void* stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* tidas_last_error(void);
 

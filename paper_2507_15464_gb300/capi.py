@@ -55,6 +55,20 @@ _SIG = {
     "tidas_fista_update": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, _P],
     "tidas_axpby": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P],
+    "tidas_psf_batch": [_P, _P, _I, _I, _P, _I, _P, _P],
+    "tidas_apod_sum": [_P, _P, ctypes.c_int64, _P, _P],
+    "tidas_gemm_bf16": [_P, _P, _I, _I, _I, _P, _I, _P, _P, _I, _P],
+    "tidas_transpose_bf16": [_P, _I, _I, _P, _P],
+    "tidas_relu_backward": [_P, _P, ctypes.c_int64, _P, _P, _P],
+    "tidas_gather_rows": [_P, _P, ctypes.c_int64, _I, _P, _P],
+    "tidas_colsum": [_P, _I, _I, _I, _P, _P],
+    "tidas_adam": [_P, _P, _P, _P, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                   ctypes.c_float, ctypes.c_float, _I, _P, _P, _P],
+    "tidas_mse": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
+    "tidas_encode": [_P, _I, _P, _P, _P, _P],
+    "tidas_forward_varying": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
+    "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
+    "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],
 }
 EXPORTED = list(_SIG) + ["tidas_last_error"]
 
@@ -157,6 +171,11 @@ def tidas_fista_update(x, y, grad, n, step, thresh, beta, stream=0):
 
 def tidas_axpby(a, b, out, n, alpha, beta, stream=0):
     return _check(load().tidas_axpby(a, b, out, n, alpha, beta, stream))
+
+
+def call(name, *args):
+    """Call any exported entry point by name, raising TidasError on failure."""
+    return _check(getattr(load(), name)(*args))
 
 
 def tidas_device_status():

@@ -403,6 +403,23 @@ int make_map_3d(CUtensorMap* map, const void* ptr, CUtensorMapDataType dt, int e
     return TIDAS_OK;
 }
 
+// 2D map over a row-major BF16 [rows][cols] matrix; box = 64 columns x box_rows
+// rows, 128-byte swizzle (the K-major UMMA operand layout)
+int make_map_2d_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled (2D) failed (%d)", (int)r);
+    return TIDAS_OK;
+}
+
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -450,12 +467,20 @@ int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int
 
 }  // namespace tidas
 
+namespace tidas {
+int read_clear_mlp_wait_flag(int* v);
+}
+
 extern "C" int tidas_device_status(int32_t* status) {
     TIDAS_REQUIRE(status, "tidas_device_status: null argument");
     TIDAS_CUDA(cudaDeviceSynchronize());
     int v = 0, zero = 0;
     TIDAS_CUDA(cudaMemcpyFromSymbol(&v, tidas::g_wait_error, sizeof(int)));
     TIDAS_CUDA(cudaMemcpyToSymbol(tidas::g_wait_error, &zero, sizeof(int)));
+    int v2 = 0;
+    int rc = tidas::read_clear_mlp_wait_flag(&v2);
+    if (rc) return rc;
+    if (v == 0) v = v2;
     *status = v;
     if (v != 0)
         return tidas::set_error(TIDAS_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", v);

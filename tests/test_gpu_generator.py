@@ -1,0 +1,152 @@
+"""GPU parity of the learned kernel generator: the tcgen05 BF16 GEMM against
+an FP64 matmul of the same BF16 values, the exact PSF batch against the
+oracle, one MLP backward pass against the FP64 reference MLP, training
+convergence, and what the trained network gains over the shift-invariant
+kernels of plain tiDAS on an unseen geometry.
+
+Tolerances: GEMM 1e-5 relative L2 (FP32 accumulation of exact BF16
+products); PSF rows 1e-5 (FP32 pulse evaluation, FP64 delays); MLP gradients
+3e-2 (the GPU rounds activations and gradients to BF16 between layers, unit
+roundoff 2^-8, while the reference stays in FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tidas_workloads import generators, presets
+
+from .gpu_helpers import host, rel_l2, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def G():
+    from paper_2507_15464_gb300 import generator
+    return generator
+
+
+@pytest.mark.parametrize("M,N,K,bias,relu", [(300, 48, 128, True, True), (256, 256, 256, True, False),
+                                             (64, 64, 256, False, False), (1000, 256, 64, True, True),
+                                             (129, 16, 64, False, True)])
+def test_gemm_bf16_matches_fp64(M, N, K, bias, relu):
+    g = G()
+    A = to_dev(generators.standard_normal((M, K), (60, M))).to(torch.bfloat16)
+    B = to_dev(generators.standard_normal((N, K), (61, N))).to(torch.bfloat16)
+    b = to_dev(generators.standard_normal((N,), (62,))) if bias else None
+    c32 = torch.empty((M, N), device="cuda")
+    c16 = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+    g.KernelMLP.gemm(A, B, M, N, K, b, relu, c32, c16, N)
+    ref = host(A) @ host(B).T + (host(b) if bias else 0.0)
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    assert rel_l2(host(c32), ref) <= 1e-5
+    assert rel_l2(host(c16), ref) <= 4e-3
+
+
+def _oracle_psf(xs, z, fnum, deg, taps=63):
+    import oracle
+    base = presets.geometry("pw128_compound")
+    dx = base["dx"]
+    geom = dict(base, angles_deg=[deg], fnum=fnum, nz=1, dz=base["dz"], z0=z - base["dz"] / 2,
+                nx=taps, x0=xs - (taps // 2) * dx - dx / 2)
+    O = oracle.Oracle(geom)
+    rf = O.synthesize([[xs, z]], [[1.0, 0.0]])
+    row = O.das_pixels(rf, np.arange(taps))
+    s = sum(O.apod(n, xs, z) for n in range(O.N))
+    return row, s
+
+
+def test_psf_batch_matches_oracle():
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = G()
+    P = DasPlan(presets.geometry("pw128_compound"))
+    cases = [(0.0, 20e-3, 1.5, 0.0), (-12.3e-3, 7.1e-3, 1.0, -11.0), (17.9e-3, 55e-3, 2.7, 14.5),
+             (3.3e-3, 33.3e-3, 1.7, 7.5)]
+    samples = np.array([[x, z, f, d * math.pi / 180.0] for x, z, f, d in cases])
+    out, norm = g.exact_kernels(P, to_dev(samples), normalise=True)
+    out, norm = host(out), host(norm)
+    for i, (x, z, f, d) in enumerate(cases):
+        row, s = _oracle_psf(x, z, f, d)
+        assert norm[i] == pytest.approx(s, rel=1e-6)
+        assert rel_l2(out[i, :63] * norm[i], row) <= 1e-5
+        assert np.all(out[i, 63:] == 0)
+
+
+def test_mlp_backward_matches_fp64_reference():
+    from oracle import mlp as orc
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = G()
+    P = DasPlan(presets.geometry("pw128_compound"))
+    s, tgt = g.training_set(P, n=256, seed=63)
+    net = g.KernelMLP(batch=256)
+    x16 = torch.empty((256, 64), dtype=torch.bfloat16, device="cuda")
+    net.encode(s, x16)
+    net.train_step(x16, tgt, lr=0.0, wd=0.0)
+    params = [(host(W16), host(b)) for W16, b in zip(net.W16, net.b)]
+    acts = orc.forward(params, host(x16))
+    grads = orc.backward(params, acts, host(tgt), 63)
+    assert float(net.loss) == pytest.approx(orc.mse(acts[-1], host(tgt), 63), rel=3e-2)
+    for l in range(4):
+        assert rel_l2(host(net.gW[l]), grads[l][0]) <= 3e-2, l
+        assert rel_l2(host(net.gb[l]), grads[l][1]) <= 3e-2, l
+
+
+def _perms(epochs, n, seed):
+    rng = np.random.default_rng([seed])
+    return to_dev(np.stack([rng.permutation(n) for _ in range(epochs)]).astype(np.int32))
+
+
+def test_training_reduces_loss():
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = G()
+    P = DasPlan(presets.geometry("pw128_compound"))
+    s, tgt = g.training_set(P, n=4096, seed=64)
+    net = g.KernelMLP(batch=256)
+    x16 = torch.empty((4096, 64), dtype=torch.bfloat16, device="cuda")
+    net.encode(s, x16)
+    losses = net.fit(x16, tgt, 30, _perms(30, 4096, 65), lr0=1e-3, log_every=1)
+    assert losses[-1][1] < 0.2 * losses[0][1]
+
+
+def test_learned_kernels_beat_shift_invariant_kernels_on_unseen_geometry():
+    # the method without the network uses one kernel per row, fitted at the
+    # centre column and applied at every lateral position; the network gives
+    # a kernel per pixel, falling back to the exact kernel where its NRMSE
+    # exceeds 2 %
+    from paper_2507_15464_gb300 import capi
+    from paper_2507_15464_gb300.ops import DasPlan, _ptr
+    g = G()
+    geom = presets.geometry("pw128_compound")
+    P = DasPlan(geom)
+    s, tgt = g.training_set(P, n=20000, seed=4)
+    net = g.KernelMLP(batch=256)
+    x16 = torch.empty((20000, 64), dtype=torch.bfloat16, device="cuda")
+    net.encode(s, x16)
+    net.fit(x16, tgt, 60, _perms(60, 20000, 5), lr0=1e-3)
+    fnum, ang = 1.7, 7.5 * math.pi / 180.0          # not a training draw
+    sub = dict(geom, nz=64, z0=geom["z0"] + 400 * geom["dz"])  # 64 rows x 512 columns
+    smp = g.grid_samples(sub, fnum, ang)
+    npix = smp.shape[0]
+    exact = g.exact_kernels(P, smp)
+    learned = net.infer(P, smp)
+    mixed = torch.empty_like(learned)
+    err_l = torch.empty((npix,), device="cuda")
+    capi.call("tidas_kernel_fallback", _ptr(learned), 64, _ptr(exact), 64, npix, 63, 0.02,
+              _ptr(mixed), 64, _ptr(err_l), 0)
+    # shift-invariant: the centre-column kernel of each row used everywhere
+    centre = host(exact).reshape(64, 512, 64)[:, 256:257, :]
+    si = np.broadcast_to(centre, (64, 512, 64)).reshape(npix, 64)
+    ex = host(exact)
+    err_si = np.linalg.norm(si[:, :63] - ex[:, :63], axis=1) / np.linalg.norm(ex[:, :63], axis=1)
+    err_mixed = np.linalg.norm(host(mixed)[:, :63] - ex[:, :63], axis=1) / \
+        np.linalg.norm(ex[:, :63], axis=1)
+    assert err_mixed.max() <= 0.02 + 1e-6
+    assert err_mixed.mean() < err_si.mean()
+    fallback = float((host(err_l) > 0.02).mean())
+    assert fallback < 1.0  # the network serves part of the grid on its own
