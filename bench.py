@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tidas", action="store_true")
     ap.add_argument("--no-fista", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--fista-iters", type=int, default=200)
     return ap.parse_args()
 
@@ -258,6 +260,13 @@ def run_ours(args):
         extra["tidas"] = bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak,
                                      bf16_peak, ms / BATCH)
 
+    # ---- learned kernel generator (training, inference, varying tiDAS)
+    if not args.no_learned and rank == 0:
+        refl16 = torch.from_numpy(np.stack([
+            generators.bernoulli_normal((g["nz"], g["nx"]), 0.02, (2, f)) for f in range(16)
+        ])).cuda()
+        extra["learned"] = bench_learned(torch, capi, generators, refl16, args.epochs)
+
     # ---- FISTA deconvolution, exact vs tiDAS operator
     if not args.no_fista and rank == 0:
         extra["fista"] = bench_fista(torch, capi, generators, args.fista_iters)
@@ -396,6 +405,82 @@ def bench_fista(torch, capi, generators, iters):
         res[name] = {"seconds": dt, "ms_per_iter": dt / iters * 1e3, "L": L, "lambda": lam,
                      "rel_err_vs_truth": rel, "x_norm2": err}
     res["speedup_tidas_gemm_resid_vs_exact"] = res["exact"]["seconds"] / res["tidas_gemm_resid"]["seconds"]
+    return res
+
+
+def bench_learned(torch, capi, generators, refl, epochs):
+    """Learned kernel generator: train on 20k exact PSFs (x, z, F# 1-3,
+    angle +-15 deg; seeds 4-5), then generate per-pixel kernels for the
+    512 x 1024 grid under an unseen geometry (F# 1.7, 7.5 deg), with exact
+    kernels as fallback above 2 % NRMSE, and drive spatially varying tiDAS."""
+    import math
+    from paper_2507_15464_gb300 import generator as gen
+    from paper_2507_15464_gb300.ops import DasPlan, _ptr, _stream, tidas_forward
+    from tidas_workloads import presets
+    geom = presets.geometry(GEOM)
+    P = DasPlan(geom)
+    res = {"train_samples": 20000, "epochs": epochs, "batch": 256}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s, tgt = gen.training_set(P, n=20000, seed=4)
+    torch.cuda.synchronize()
+    res["training_set_seconds"] = time.perf_counter() - t0
+    net = gen.KernelMLP(batch=256)
+    x16 = torch.empty((20000, 64), dtype=torch.bfloat16, device="cuda")
+    net.encode(s, x16)
+    rng = np.random.default_rng([5])
+    perms = torch.from_numpy(np.stack([rng.permutation(20000) for _ in range(epochs)])
+                             .astype(np.int32)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.fit(x16, tgt, epochs, perms, lr0=1e-3, log_every=max(1, epochs // 4))
+    torch.cuda.synchronize()
+    res["training_seconds"] = time.perf_counter() - t0
+    res["loss_curve"] = losses
+    fnum, ang = 1.7, 7.5 * math.pi / 180.0
+    smp = gen.grid_samples(geom, fnum, ang)
+    npix = smp.shape[0]
+    stream = torch.cuda.current_stream()
+    learned = net.infer(P, smp)
+    exact = gen.exact_kernels(P, smp)
+    ms_inf = time_steps(torch, lambda: net.infer(P, smp), 3, 1, stream)
+    ms_exact = time_steps(torch, lambda: gen.exact_kernels(P, smp), 2, 1, stream)
+    flops = 2.0 * npix * (4 * 256 + 2 * 256 * 256 + 256 * 63)
+    res["inference"] = {"kernels": npix, "ms": ms_inf, "kernels_per_s": npix / (ms_inf * 1e-3),
+                        "tensor": {"achieved_tflops": flops / (ms_inf * 1e-3) / 1e12,
+                                   "peak_tflops": peaks()[1],
+                                   "frac": flops / (ms_inf * 1e-3) / 1e12 / peaks()[1]},
+                        "exact_psf_ms": ms_exact, "speedup_vs_exact_fit": ms_exact / ms_inf}
+    mixed = torch.empty_like(learned)
+    err = torch.empty((npix,), device="cuda")
+    capi.call("tidas_kernel_fallback", _ptr(learned), 64, _ptr(exact), 64, npix, 63, 0.02,
+              _ptr(mixed), 64, _ptr(err), _stream())
+    e = err.cpu().numpy()
+    ex = exact.cpu().numpy()[:, :63].reshape(geom["nz"], geom["nx"], 63)
+    si = np.broadcast_to(ex[:, geom["nx"] // 2:geom["nx"] // 2 + 1, :], ex.shape)
+    e_si = (np.linalg.norm(si - ex, axis=2) / np.linalg.norm(ex, axis=2)).ravel()
+    res["kernel_nrmse"] = {"learned_mean": float(e.mean()), "learned_median": float(np.median(e)),
+                           "fallback_fraction": float((e > 0.02).mean()),
+                           "shift_invariant_mean": float(e_si.mean())}
+    # images: spatially varying tiDAS with the mixed kernels vs exact single-angle DAS
+    g1 = dict(geom, angles_deg=[7.5], fnum=fnum)
+    P1 = DasPlan(g1)
+    nf = refl.shape[0]
+    out = torch.empty_like(refl)
+    capi.call("tidas_forward_varying", _ptr(mixed), 64, 63, geom["nz"], geom["nx"], _ptr(refl),
+              _ptr(out), nf, _stream())
+    ms_var = time_steps(torch, lambda: capi.call("tidas_forward_varying", _ptr(mixed), 64, 63,
+                                                  geom["nz"], geom["nx"], _ptr(refl), _ptr(out),
+                                                  nf, _stream()), 3, 1, stream)
+    res["varying_tidas"] = {"frames": nf, "ms": ms_var,
+                            "mpix_s": nf * npix / (ms_var * 1e-3) / 1e6}
+    das = P1.forward(P1.synthesize_grid(refl[:1].contiguous()))
+    k_row, _ = P1.fit_kernels(63)
+    y_si = tidas_forward(k_row, refl[:1].contiguous())
+    d = das[0].double()
+    res["image_nrmse_vs_exact_das"] = {
+        "learned_varying": float((out[0].double() - d).norm() / d.norm()),
+        "shift_invariant_rows": float((y_si[0].double() - d).norm() / d.norm())}
     return res
 
 
