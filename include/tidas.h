@@ -86,6 +86,15 @@ int das_plan_create(const das_params* params, das_plan* out_plan);
 /* Free the plan's device tables.  Waits for the device first.  NULL is a no-op. */
 int das_plan_destroy(das_plan plan);
 
+/* Plan options.  DAS_OPT_TENSOR_CORES: 1 (default) runs das_forward of FP16
+ * plans on the tcgen05 tensor cores when n_frames >= 16 and every
+ * (16 x 8-pixel tile, angle, element) window of samples fits 64 samples
+ * (checked when the plan is built); 0 keeps every batch on CUDA cores.  The
+ * tensor-core path rounds the apodized interpolation weights to FP16
+ * (relative 2^-11). */
+#define DAS_OPT_TENSOR_CORES 1
+int das_plan_set_option(das_plan plan, int32_t option, int32_t value);
+
 /* Channel data of point scatterers under the Born approximation, Eq. (2.1):
  * rf[f][a][n][k] = sum_j Re(A_fj * p(t_k - tau_a,n(x_fj, z_fj))), with the
  * Gaussian-modulated pulse p (6 dB band f0(1 +- frac_bw/2), truncated at the

@@ -39,6 +39,7 @@ _I = ctypes.c_int32
 _SIG = {
     "das_plan_create": [ctypes.POINTER(das_params), ctypes.POINTER(ctypes.c_void_p)],
     "das_plan_destroy": [_P],
+    "das_plan_set_option": [_P, _I, _I],
     "das_synthesize": [_P, _P, _P, _I, _I, _P, _P],
     "das_synthesize_grid": [_P, _P, _P, _I, _P],
     "das_synthesize_adjoint": [_P, _P, _P, _I, _P],

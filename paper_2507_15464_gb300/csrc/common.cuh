@@ -61,6 +61,12 @@ struct Plan {
     const double* d_sncs;   // device [A][2]: sin, cos of each angle (host libm values)
     bool taps_in_range;     // every interpolation tap of every pixel lies in [0, n_samples)
     double thalf_samples, beta_samples, wcar;
+    // tensor-core DAS of FP16 plans: per-(tile, angle, element) sample windows
+    int* tc_tab = nullptr;
+    int2* tc_range = nullptr;
+    int tc_tiles_x = 0, tc_tiles = 0;
+    bool tc_ok = false;     // every window fits the 64-sample operand tile
+    int tc_mode = 1;        // 0: CUDA cores only, 1: tensor cores for >= 16 FP16 frames
 };
 
 // ---------------------------------------------------------- device helpers
@@ -116,6 +122,8 @@ __device__ __forceinline__ void store_rf(__half* p, float v) { *p = __float2half
 namespace tidas {
 int launch_delay_table(const Plan& P, int angle, int32_t* idx, float* frac, cudaStream_t st);
 int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
+int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
+int das_tc_prepare(Plan& P);
 int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaStream_t st);
 int launch_synthesize(const Plan& P, const double* pos, const float* amp, int n_scat, int nf,
                       void* rf, cudaStream_t st);

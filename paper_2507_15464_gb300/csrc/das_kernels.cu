@@ -182,6 +182,11 @@ static void das_forward_dispatch(const Plan& P, const void* rf, float* img, int 
 }
 
 int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st) {
+    // batches of FP16 channel data go to the tensor cores (frames are the
+    // MMA's N dimension); small batches and FP32 data stay on CUDA cores
+    if (P.dev.rf_dtype == TIDAS_RF_F16 && P.tc_ok && P.tc_mode == 1 && nf >= 16 &&
+        ((uintptr_t)rf % 16) == 0)
+        return launch_das_tc(P, rf, img, nf, st);
     if (P.dev.rf_dtype == TIDAS_RF_F16) das_forward_dispatch<__half>(P, rf, img, nf, st);
     else das_forward_dispatch<float>(P, rf, img, nf, st);
     return check_launch("das_forward_kernel");

@@ -237,8 +237,30 @@ extern "C" int das_plan_create(const das_params* params, das_plan* out_plan) {
     d.xs = (const float*)(b + o_xs);
     d.elem0_s = (float)(-0.5 * (double)(NE - 1) * p.pitch * k);
     d.pitch_s = (float)(p.pitch * k);
+    if (p.rf_dtype == TIDAS_RF_F16 && p.n_samples % 8 == 0) {
+        // sample windows of the tensor-core DAS; without them the CUDA-core
+        // kernel serves every batch
+        int rc = das_tc_prepare(*P);
+        if (rc) {
+            cudaFree(P->tc_tab);
+            cudaFree(P->blob);
+            delete P;
+            return rc;
+        }
+    }
     *out_plan = (das_plan)P;
     return TIDAS_OK;
+}
+
+extern "C" int das_plan_set_option(das_plan plan, int32_t option, int32_t value) {
+    TIDAS_REQUIRE(plan, "das_plan_set_option: null plan");
+    Plan* P = (Plan*)plan;
+    if (option == DAS_OPT_TENSOR_CORES) {
+        TIDAS_REQUIRE(value == 0 || value == 1, "das_plan_set_option: value must be 0 or 1");
+        P->tc_mode = value;
+        return TIDAS_OK;
+    }
+    return set_error(TIDAS_ERR_ARG, "das_plan_set_option: unknown option %d", option);
 }
 
 extern "C" int das_plan_destroy(das_plan plan) {
@@ -246,6 +268,10 @@ extern "C" int das_plan_destroy(das_plan plan) {
     Plan* P = (Plan*)plan;
     cudaError_t e = cudaDeviceSynchronize();
     cudaError_t e2 = cudaFree(P->blob);
+    if (P->tc_tab) {
+        cudaError_t e3 = cudaFree(P->tc_tab);
+        if (e2 == cudaSuccess) e2 = e3;
+    }
     delete P;
     if (e != cudaSuccess) return check_cuda(e, "cudaDeviceSynchronize(plan destroy)");
     return check_cuda(e2, "cudaFree(plan tables)");

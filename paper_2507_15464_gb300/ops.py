@@ -53,6 +53,10 @@ class DasPlan:
         self.A, self.N, self.S = p.n_angles, p.n_elem, p.n_samples
         self.nx, self.nz = p.nx, p.nz
 
+    def set_tensor_cores(self, on: bool):
+        """Route batches of >= 16 FP16 frames to the tensor-core DAS (default) or not."""
+        capi.call("das_plan_set_option", self.handle, 1, 1 if on else 0)
+
     def close(self):
         if self.handle:
             capi.das_plan_destroy(self.handle)

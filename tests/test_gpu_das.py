@@ -122,6 +122,13 @@ def test_das_compound_fp16_channel_data():
         assert rel_l2(img[f].ravel()[pix], O.das_pixels(rf32[f], pix)) <= TOL16
 
 
+# The tensor-core path (>= 16 FP16 frames) rounds the apodized interpolation
+# weights to FP16: relative error <= 2^-11 per weight, ~2^-11/sqrt(3) = 2.8e-4
+# rms over the ~650 terms of a pixel; bound 1e-3 against the oracle on the
+# same channel data (and 5e-3 against unquantised data).
+TOL_TC = 1e-3
+
+
 def test_das_full_batch_fp16_sampled_frames():
     # the benchmark's launch configuration: 64 frames of FP16 channel data
     g = presets.geometry("pw128_compound")
@@ -130,12 +137,41 @@ def test_das_full_batch_fp16_sampled_frames():
     rf = np.empty((B, 11, 128, 4096), np.float16)
     for f in range(B):
         rf[f] = generators.standard_normal((11, 128, 4096), (21, f), np.float16)
-    img = host(P16.forward(to_dev(rf)))
+    x = to_dev(rf)
+    img = host(P16.forward(x))            # tensor cores
+    P16.set_tensor_cores(False)
+    img_cc = host(P16.forward(x))         # CUDA cores
     rng = np.random.default_rng(9)
     for f in (0, 37, B - 1):
         pix = rng.choice(g["nx"] * g["nz"], 600, replace=False)
         ref = O.das_pixels(rf[f].astype(np.float64), pix)
-        assert rel_l2(img[f].ravel()[pix], ref) <= TOL32
+        assert rel_l2(img[f].ravel()[pix], ref) <= TOL_TC
+        assert rel_l2(img_cc[f].ravel()[pix], ref) <= TOL32
+    assert rel_l2(img, img_cc) <= TOL_TC
+
+
+@pytest.mark.parametrize("name,nf,over", [
+    ("pw128_compound", 16, {}), ("pw128_compound", 20, {}),
+    ("pw64_single", 16, {}), ("pw64_single", 17, dict(nx=100, nz=77, n_samples=1104)),
+    ("pw64_single", 33, dict(interp=1, nx=64, nz=40, z0=6e-3))])
+def test_das_tensor_core_path(name, nf, over):
+    # ragged pixel tiles, ragged frame tiles, out-of-record windows (TMA zero
+    # fill), linear and cubic interpolation
+    g = presets.geometry(name, **over)
+    P16, O = plan(g, torch.float16), oracle(g)
+    S = g["n_samples"]
+    rf = generators.standard_normal((nf, len(g["angles_deg"]), g["n_elem"], S), (29, nf),
+                                    np.float16)
+    x = to_dev(rf)
+    img = host(P16.forward(x))
+    P16.set_tensor_cores(False)
+    img_cc = host(P16.forward(x))
+    assert rel_l2(img, img_cc) <= TOL_TC
+    rng = np.random.default_rng(10)
+    for f in (0, nf - 1):
+        pix = rng.choice(g["nx"] * g["nz"], min(800, g["nx"] * g["nz"]), replace=False)
+        ref = O.das_pixels(rf[f].astype(np.float64), pix)
+        assert rel_l2(img[f].ravel()[pix], ref) <= TOL_TC
 
 
 @pytest.mark.parametrize("interp", [0, 1])
