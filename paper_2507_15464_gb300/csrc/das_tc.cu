@@ -15,8 +15,8 @@
 // Warp roles: warp 0 streams channel windows [NF frames x 64 samples] by
 // TMA (zero fill outside the record) through a deep ring, so that the L2
 // latency of the many small windows is covered; warp 1 owns tensor memory
-// and issues the MMAs; warps 2-5 build W_an in a shallower ring, one pixel
-// per thread, writing and later erasing whole swizzled 16-byte chunks (the
+// and issues the MMAs; warps 2-9 build W_an (two groups of four warps on
+// alternate pairs), one pixel per thread, writing and later erasing whole swizzled 16-byte chunks (the
 // swizzle spreads the 32 rows of a warp over distinct banks), and finally
 // drain the accumulators.
 #include <climits>
@@ -42,15 +42,14 @@ namespace dtc {
 constexpr int kTX = 16, kTZ = 8;          // pixel tile
 constexpr int kM = kTX * kTZ;             // 128 = UMMA M
 constexpr int kKW = 64;                   // window columns (one 128-byte swizzle row)
-constexpr int kWStages = 3;               // weight tiles in flight
-constexpr int kRStages = 6;               // channel windows in flight
+constexpr int kWStages = 4;               // weight tiles in flight (a power of two)
+constexpr int kRStages = 3;               // channel windows in flight
 constexpr int kWBytes = kM * kKW * 2;     // 16 KB
-// channel stage = NF frames x 128 bytes, sized per launch (two CTAs share an
-// SM when NF <= 64)
+// channel stage = NF frames x 128 bytes, sized per launch
 __host__ __device__ constexpr int r_bytes(int NF) { return (NF < 32 ? 32 : NF) * kKW * 2; }
-__host__ __device__ constexpr size_t smem_bytes(int NF, int A) {
+__host__ __device__ constexpr size_t smem_bytes(int NF, int A, int NE) {
     return 1024 + (size_t)kWStages * kWBytes + (size_t)kRStages * r_bytes(NF) + 1024 +
-           (size_t)kWStages * kM * 4 + (size_t)A * kM * 8;
+           (size_t)kWStages * kM * 4 + (size_t)A * kM * 8 + (size_t)A * NE * 4;
 }
 }  // namespace dtc
 
@@ -108,7 +107,7 @@ __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __res
     }
 }
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     das_tc_kernel(const __grid_constant__ CUtensorMap tmap, DasDev d, const int* __restrict__ tab,
                   const int2* __restrict__ range, int tiles_x, int nf, int NF,
                   float* __restrict__ img) {
@@ -127,6 +126,7 @@ __global__ void __launch_bounds__(192, 1)
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
     int* prev = (int*)((uint8_t*)full_r + 1024);              // [kWStages][kM]
     int2* s_base = (int2*)(prev + kWStages * kM);              // [A][kM]: transmit split
+    int* s_tab = (int*)(s_base + d.n_angles * kM);             // [pair]: window entries
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x;
@@ -158,6 +158,13 @@ __global__ void __launch_bounds__(192, 1)
     for (int i = threadIdx.x; i < kWStages * kWBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(sW)[i] = make_uint4(0, 0, 0, 0);
     for (int i = threadIdx.x; i < kWStages * kM; i += blockDim.x) prev[i] = -1;
+    // this tile's window entries (pair order: element-major, angle-minor), so
+    // that no role waits on a global load per pair
+    {
+        const int* tt = tab + (size_t)tile * A * NE;
+        for (int i = threadIdx.x; i < npairs; i += blockDim.x)
+            s_tab[i] = __ldg(tt + (i % A) * NE + n_lo + i / A);
+    }
     if (warp == 1) {
         tmem_alloc(tmem_slot, tcols);
         tmem_relinquish();
@@ -167,7 +174,6 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int* ttab = tab + (size_t)tile * A * NE;
 
     if (warp == 0) {
         // ------------------------------------------ channel windows by TMA
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t st = 0, ph = 0;
             for (int q = 0; q < npairs && !*s_abort; ++q) {
                 const int n = n_lo + q / A, a = q % A;
-                const int e = __ldg(ttab + a * NE + n);
+                const int e = s_tab[q];
                 if (!mbar_wait(&empty_r[st], ph ^ 1, &g_das_tc_wait_error, 301)) {
                     *s_abort = 1;
                     break;
@@ -192,8 +198,7 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t rs = 0, rph = 0, ws = 0, wph = 0;
             bool first = true;
             for (int q = 0; q < npairs && !*s_abort; ++q) {
-                const int n = n_lo + q / A, a = q % A;
-                const int e = __ldg(ttab + a * NE + n);
+                const int e = s_tab[q];
                 const bool ok = mbar_wait(&full_w[ws], wph, &g_das_tc_wait_error, 302) &&
                                 mbar_wait(&full_r[rs], rph, &g_das_tc_wait_error, 303);
                 if (!ok) {
@@ -217,38 +222,49 @@ __global__ void __launch_bounds__(192, 1)
         }
         __syncwarp();
     } else {
-        // ------------------------------ weight tiles, one pixel per thread
+        // ------------ weight tiles, one pixel per thread; two groups of four
+        // warps take alternate pairs (stages g and g + 2 of the ring)
+        const int grp = (warp - 2) >> 2;
         const int m = 32 * (warp & 3) + lane;  // tensor-memory lane = pixel row of W
-        const int ix = tx * kTX + (m % kTX), iz = tz * kTZ + m / kTX;
+        const int col = m % kTX;
+        const int ix = tx * kTX + col, iz = tz * kTZ + m / kTX;
         const bool valid = ix < d.nx && iz < d.nz;
         const int ixc = valid ? ix : 0, izc = valid ? iz : 0;
         const float zs = __ldg(d.zs + izc);
-        for (int a = 0; a < A; ++a) {
-            const int bi = __ldg(d.bxi + a * d.nx + ixc) + __ldg(d.bzi + a * d.nz + izc);
-            const float bf = __ldg(d.bxf + a * d.nx + ixc) + __ldg(d.bzf + a * d.nz + izc);
-            s_base[a * kM + m] = make_int2(bi, __float_as_int(bf));
+        if (grp == 0) {
+            for (int a = 0; a < A; ++a) {
+                const int bi = __ldg(d.bxi + a * d.nx + ixc) + __ldg(d.bzi + a * d.nz + izc);
+                const float bf = __ldg(d.bxf + a * d.nx + ixc) + __ldg(d.bzf + a * d.nz + izc);
+                s_base[a * kM + m] = make_int2(bi, __float_as_int(bf));
+            }
         }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // both groups read s_base
+        uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
+        const int swz = m & 7;
         float w = 0.f, exc = 0.f;
-        uint32_t st = 0, ph = 0;
-        for (int q = 0; q < npairs && !*s_abort; ++q) {
-            const int n = n_lo + q / A, a = q % A;
-            if (a == 0) {
+        int cur_n = -1;
+        int n = n_lo + grp / A, a = grp % A;
+        for (int q = grp; q < npairs && !*s_abort; q += 2) {
+            if (n != cur_n) {
+                cur_n = n;
                 const float dxs = __ldg(d.dxs + (size_t)n * d.nx + ixc);
                 w = valid ? apod_weight(dxs, zs, d.fnum) : 0.f;
                 exc = rx_excess(dxs, zs);
             }
-            const int e = __ldg(ttab + a * NE + n);
+            const int st = q & (kWStages - 1);
+            const uint32_t ph = (uint32_t)(q / kWStages) & 1u;
+            const int e = s_tab[q];
             const int k0 = e >> 3, lim = (e & 7) * 16;
-            if (!mbar_wait(&empty_w[st], ph ^ 1, &g_das_tc_wait_error, 304)) {
+            if (!mbar_wait(&empty_w[st], ph ^ 1u, &g_das_tc_wait_error, 304)) {
                 *s_abort = 1;
                 break;
             }
-            uint8_t* W = sW + st * kWBytes;
+            uint8_t* W = rowp + st * kWBytes;
             const int pc = prev[st * kM + m];
             if (pc >= 0) {
-                *reinterpret_cast<uint4*>(W + sw128_offset(m, (pc >> 3) * 8)) = make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4*>(W + ((((pc >> 3)) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
                 if ((pc & 7) > 4)
-                    *reinterpret_cast<uint4*>(W + sw128_offset(m, (pc >> 3) * 8 + 8)) =
+                    *reinterpret_cast<uint4*>(W + ((((pc >> 3) + 1) ^ swz) << 4)) =
                         make_uint4(0, 0, 0, 0);
             }
             int nc = -1;
@@ -277,9 +293,8 @@ __global__ void __launch_bounds__(192, 1)
                                         ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
                     uint4 lo, hi;
                     place4(pk, c & 7, lo, hi);
-                    *reinterpret_cast<uint4*>(W + sw128_offset(m, (c >> 3) * 8)) = lo;
-                    if ((c & 7) > 4)
-                        *reinterpret_cast<uint4*>(W + sw128_offset(m, (c >> 3) * 8 + 8)) = hi;
+                    *reinterpret_cast<uint4*>(W + (((c >> 3) ^ swz) << 4)) = lo;
+                    if ((c & 7) > 4) *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
                     nc = c;
                 }
             }
@@ -287,8 +302,13 @@ __global__ void __launch_bounds__(192, 1)
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_w[st]);
-            if (++st == kWStages) { st = 0; ph ^= 1; }
+            a += 2;
+            while (a >= A) {
+                a -= A;
+                ++n;
+            }
         }
+        if (grp == 0) {  // epilogue: the first group holds every tensor-memory lane
         // --------------------------------------------------- epilogue
         bool have = npairs > 0;
         if (have && !mbar_wait(done, 0, &g_das_tc_wait_error, 305)) {
@@ -312,6 +332,7 @@ __global__ void __launch_bounds__(192, 1)
                 for (int e2 = 0; e2 < 32; ++e2)
                     if (f0 + j + e2 < nf && j + e2 < NF) dst[(size_t)e2 * plane] = __uint_as_float(r[e2]);
             }
+        }
         }
     }
     tc_fence_before();
@@ -347,23 +368,29 @@ int das_tc_prepare(Plan& P) {
     if (rc) return rc;
     int bad = 0;
     TIDAS_CUDA(cudaMemcpy(&bad, d_bad, 4, cudaMemcpyDeviceToHost));
-    P.tc_ok = (bad == 0) && dtc::smem_bytes(128, d.n_angles) <= 227 * 1024;
+    P.tc_ok = (bad == 0) && dtc::smem_bytes(16, d.n_angles, d.n_elem) <= 227 * 1024;
     return TIDAS_OK;
 }
 
 int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st) {
     using namespace dtc;
     const DasDev& d = P.dev;
-    const int NF = nf >= 128 ? 128 : (nf >= 64 ? 64 : (nf >= 32 ? 32 : 16));
+    // the widest frame tile (MMA N) that the batch fills and shared memory holds
+    int NF = 16;
+    for (int c = 128; c > 16; c /= 2)
+        if (nf >= c && smem_bytes(c, d.n_angles, d.n_elem) <= 227 * 1024) {
+            NF = c;
+            break;
+        }
     CUtensorMap map;
     // channel data as [frames][angles * elements][samples]: box 64 samples x 1 row x NF frames
     int rc = make_map_3d(&map, rf, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, d.n_angles * d.n_elem,
                          d.n_samples, nf, kKW, NF, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
-    const size_t smem = smem_bytes(NF, d.n_angles);
+    const size_t smem = smem_bytes(NF, d.n_angles, d.n_elem);
     cudaFuncSetAttribute(das_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(P.tc_tiles, (nf + NF - 1) / NF);
-    das_tc_kernel<<<grid, 192, smem, st>>>(map, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF,
+    das_tc_kernel<<<grid, 320, smem, st>>>(map, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF,
                                            img);
     return check_launch("das_tc_kernel");
 }
