@@ -221,10 +221,16 @@ def run_ours(args):
     sms = props.multi_processor_count
     fp32_peak = sms * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s at the maximum SM clock
     alg_bytes = rf.numel() * 2 + img.numel() * 4
+    # DRAM bytes of one launch of the timed kernel, from the ncu capture summarised
+    # in profiles/das_tc_kernel_pw128_compound_64frames_f16.md (same kernel, same
+    # 64-frame launch); None whenever the kernel changes after that capture
+    traffic = 950.2e6 if BATCH == 64 else None
     roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
-            "unit": "TFLOP/s", "traffic": None,
+            "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
             "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x 2070 MHz" % sms,
-            "work": "%.4g updates x 10 flop (cubic taps + apodization)" % updates}
+            "work": "%.4g updates x 10 flop (cubic taps + apodization)" % updates,
+            "note": "tensor-core kernel limited by the issue rate of its weight-building "
+                    "warps; tensor pipe 16.7 % busy (ncu)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     hbm = {"achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
            "peak_source": peak_src, "bytes_per_launch": alg_bytes}
