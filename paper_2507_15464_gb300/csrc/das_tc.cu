@@ -244,10 +244,16 @@ __global__ void __launch_bounds__(320, 1)
         float w = 0.f, exc = 0.f;
         int cur_n = -1;
         int n = n_lo + grp / A, a = grp % A;
+        // lateral offset of the group's next element, loaded one element ahead
+        // (a single-angle plan gives each group every other element)
+        int pre_n = n;
+        float dxs_next = n <= n_hi ? __ldg(d.dxs + (size_t)n * d.nx + ixc) : 0.f;
         for (int q = grp; q < npairs && !*s_abort; q += 2) {
             if (n != cur_n) {
                 cur_n = n;
-                const float dxs = __ldg(d.dxs + (size_t)n * d.nx + ixc);
+                const float dxs = n == pre_n ? dxs_next : __ldg(d.dxs + (size_t)n * d.nx + ixc);
+                pre_n = n + (A == 1 ? 2 : 1);
+                if (pre_n <= n_hi) dxs_next = __ldg(d.dxs + (size_t)pre_n * d.nx + ixc);
                 w = valid ? apod_weight(dxs, zs, d.fnum) : 0.f;
                 exc = rx_excess(dxs, zs);
             }
