@@ -88,10 +88,13 @@ int das_plan_destroy(das_plan plan);
 
 /* Plan options.  DAS_OPT_TENSOR_CORES: 1 (default) runs das_forward of FP16
  * plans on the tcgen05 tensor cores when n_frames >= 16 and every
- * (16 x 8-pixel tile, angle, element) window of samples fits 64 samples
+ * (32 x 4-pixel tile, angle, element) window of samples fits 64 samples
  * (checked when the plan is built); 0 keeps every batch on CUDA cores.  The
  * tensor-core path rounds the apodized interpolation weights to FP16
- * (relative 2^-11). */
+ * (relative 2^-11).  It first repacks the batch into a staging buffer that
+ * the plan owns (about the size of the channel data; allocated on first use
+ * and grown when a larger batch arrives), so das_forward calls on one FP16
+ * plan must not overlap in time (issue them on one stream, or synchronise). */
 #define DAS_OPT_TENSOR_CORES 1
 int das_plan_set_option(das_plan plan, int32_t option, int32_t value);
 

@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "tidas.h"
 
 // ---------------------------------------------------------------- errors
@@ -67,6 +69,10 @@ struct Plan {
     int tc_tiles_x = 0, tc_tiles = 0;
     bool tc_ok = false;     // every window fits the 64-sample operand tile
     int tc_mode = 1;        // 0: CUDA cores only, 1: tensor cores for >= 16 FP16 frames
+    // staging buffer of the repacked channel data (tensor-core DAS), grown on demand
+    mutable void* tc_ws = nullptr;
+    mutable size_t tc_ws_bytes = 0;
+    mutable std::mutex tc_ws_mutex;
 };
 
 // ---------------------------------------------------------- device helpers

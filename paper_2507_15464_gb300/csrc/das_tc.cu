@@ -1,25 +1,45 @@
 // Delay and Sum (Eq. (2.2)) for batches of FP16 channel data on the tcgen05
 // tensor cores.
 //
-// For a tile of 128 pixels (16 columns x 8 rows) and a tile of NF frames,
+// For a tile of 128 pixels (32 columns x 4 rows) and a tile of NF frames,
 //     img[p, f] = sum_{a,n} sum_k W_an[p, k] * rf[f, a, n, k0_an + k],
 // where row p of W_an holds the apodized interpolation weights
 // w_n(p) * K(u - m) of the (2 or 4) samples m that pixel p reads, placed at
-// columns m - k0_an.  Over one tile every (angle, element) pair reads a
-// window of fewer than 64 consecutive samples, so each pair is a dense
-// 128 x NF x (<= 64) FP16 contraction accumulated in FP32 tensor memory.
-// The window start k0_an (a multiple of 8, for TMA alignment) and the
-// number of 16-column K-steps are tabulated per (tile, angle, element) when
-// the plan is created.
+// columns m - k0_an.  Over one tile every (angle, element) pair reads fewer
+// than 64 consecutive samples, so each pair is a dense 128 x NF x (16 s)
+// FP16 contraction (s = 1..4 K-steps) accumulated in FP32 tensor memory.  The
+// window start k0_an (a multiple of 8) and s are tabulated per (tile, angle,
+// element) when the plan is created.
 //
-// Warp roles: warp 0 streams channel windows [NF frames x 64 samples] by
-// TMA (zero fill outside the record) through a deep ring, so that the L2
-// latency of the many small windows is covered; warp 1 owns tensor memory
-// and issues the MMAs; warps 2-9 build W_an (two groups of four warps on
-// alternate pairs), one pixel per thread, writing and later erasing whole swizzled 16-byte chunks (the
-// swizzle spreads the 32 rows of a warp over distinct banks), and finally
-// drain the accumulators.
+// Channel data.  A TMA box of NF frames x 64 samples is NF separate rows of
+// the [frame][angle, element][sample] layout, and the copy engine spends
+// about as long on a row as on a kilobyte of contiguous data.  So each batch
+// is first repacked (das_tc_pack_kernel, one HBM-bound pass) into
+// [frame tile][angle, element][sample][NF frames] with the 16-byte chunks of
+// every sample row already permuted into the MMA's swizzled MN-major operand
+// layout, and 64 zero samples before and after each record.  The s K-steps
+// of a pair are then s x 16 consecutive sample rows, one contiguous
+// cp.async.bulk copy.
+//
+// Warp roles (12 warps, two groups):
+//  - warps 0, 1: producers of group 0 / group 1: one bulk copy per pair into
+//    the group's ring of K-step chunks (as many pairs in flight as the ring
+//    holds).  Warp 0 also owns tensor memory.
+//  - warps 2-5 / 6-9: the builders of group 0 / group 1.  The groups take
+//    alternate pairs.  Every thread owns one pixel (one row of W_an, one
+//    tensor-memory lane): it erases the 16-byte chunks it wrote two pairs
+//    ago and writes its four weights as swizzled chunks of a 128-byte-swizzled
+//    K-major weight tile (two per group).
+//  - warps 10, 11: the MMA warps of group 0 / group 1.  Builders and MMA warp
+//    meet at a named barrier once per pair; then the MMA warp issues that
+//    pair's K-steps into the group's own accumulator while the builders write
+//    the next pair, and one tcgen05.commit per pair frees both the weight tile
+//    and the pair's chunks.  A single thread issues one tcgen05.mma about
+//    every 100 cycles, while a 128 x 64 x 16 step occupies the tensor pipe
+//    for about 50, so two issuing threads per CTA (four per SM) keep it fed.
+// The epilogue sums the two accumulators.
 #include <climits>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -39,19 +59,102 @@ int read_clear_das_tc_wait_flag(int* v) {
 }
 
 namespace dtc {
-constexpr int kTX = 16, kTZ = 8;          // pixel tile
+constexpr int kTX = 32, kTZ = 4;          // pixel tile: one row of 32 per warp
 constexpr int kM = kTX * kTZ;             // 128 = UMMA M
-constexpr int kKW = 64;                   // window columns (one 128-byte swizzle row)
-constexpr int kWStages = 4;               // weight tiles in flight (a power of two)
-constexpr int kRStages = 3;               // channel windows in flight
+constexpr int kKW = 64;                   // weight-tile columns (one 128-byte swizzle row)
+constexpr int kKC = 16;                   // samples per K-step chunk
+constexpr int kMaxSteps = kKW / kKC;
+constexpr int kPad = 64;                  // zero samples before and after each packed record
+constexpr int kPackS = 64;                // samples per pack block
+constexpr int kGroups = 2;                // builder groups, one accumulator each
+constexpr int kWTiles = 2 * kGroups;      // weight tiles: two per group
 constexpr int kWBytes = kM * kKW * 2;     // 16 KB
-// channel stage = NF frames x 128 bytes, sized per launch
-__host__ __device__ constexpr int r_bytes(int NF) { return (NF < 32 ? 32 : NF) * kKW * 2; }
-__host__ __device__ constexpr size_t smem_bytes(int NF, int A, int NE) {
-    return 1024 + (size_t)kWStages * kWBytes + (size_t)kRStages * r_bytes(NF) + 1024 +
-           (size_t)kWStages * kM * 4 + (size_t)A * kM * 8 + (size_t)A * NE * 4;
+constexpr int kPairSlots = 8;             // pairs of a group in flight (barrier slots)
+constexpr int kMinChunks = 6, kMaxChunks = 32;  // chunks per group ring
+// per group: one producer warp, four builder warps, one MMA warp
+constexpr int kBuilderWarp0 = kGroups;            // warps [0, kGroups): producers
+constexpr int kMmaWarp0 = kGroups + 4 * kGroups;  // warps [kMmaWarp0, kWarps): MMA warps
+constexpr int kWarps = kMmaWarp0 + kGroups;
+constexpr int kThreads = 32 * kWarps;
+static_assert(kWarps == 6 * kGroups && kGroups == 2, "warp roles assume two groups of six warps");
+constexpr int kEpiBarCount = 32 * 5 * kGroups;    // builders wait, MMA warps arrive
+constexpr size_t kSmemTwoPerSM = 115712;  // (228 KB - 2 x 1 KB reserved) / 2
+constexpr size_t kSmemMax = 227 * 1024;
+// one K-step chunk = 16 sample rows of NF frames
+__host__ __device__ constexpr int chunk_bytes(int NF) { return kKC * NF * 2; }
+// align | weight tiles | chunk rings | barriers, flags (1 KB) | prev [kWTiles][kM] int8 |
+// transmit split [A][kM] int2 | window entries [A * NE] int16
+__host__ __device__ constexpr size_t fixed_bytes(int A, int NE) {
+    return 1024 + (size_t)kWTiles * kWBytes + 1024 + (size_t)kWTiles * kM + (size_t)A * kM * 8 +
+           (((size_t)A * NE * 2 + 15) & ~(size_t)15);
+}
+__host__ __device__ constexpr size_t smem_bytes(int NF, int C, int A, int NE) {
+    return fixed_bytes(A, NE) + (size_t)kGroups * C * chunk_bytes(NF);
+}
+// packed record length (samples, margins included)
+__host__ __device__ constexpr int packed_len(int S) {
+    return (S + kPackS - 1) / kPackS * kPackS + 2 * kPad;
 }
 }  // namespace dtc
+
+// Swizzled position of 16-byte chunk c in sample row k of an MN-major operand
+// whose rows hold NF frames (NF * 2 bytes): the 128-, 64- or 32-byte swizzle
+// XORs the chunk index with bits of the row index (address bits 7.. into
+// bits 4..), repeating every 8 rows.
+__host__ __device__ __forceinline__ int mn_swizzle(int c, int k, int NF) {
+    return NF == 64 ? c ^ (k & 7) : NF == 32 ? c ^ ((k >> 1) & 3) : c ^ ((k >> 2) & 1);
+}
+
+// [nf][R][S] FP16 -> [FT][R][Sp][NF] FP16, sample s at s + kPad, frames past
+// nf and samples outside [0, S) zero, chunks swizzled (mn_swizzle).  One
+// block per (frame tile, row, 64 samples); S is a multiple of 8.
+__global__ void __launch_bounds__(256) das_tc_pack_kernel(const __half* __restrict__ rf,
+                                                          __half* __restrict__ out, int nf, int R,
+                                                          int S, int Sp, int NF) {
+    using namespace dtc;
+    __shared__ uint16_t tile[kPackS][64 + 2];
+    const int nsb = Sp / kPackS;
+    const int sb = blockIdx.x % nsb;
+    const int row = (blockIdx.x / nsb) % R;
+    const int ft = blockIdx.x / (nsb * R);
+    const int s0 = sb * kPackS - kPad;
+    // load NF frames x 64 samples as 16-byte chunks of 8 samples
+    for (int i = threadIdx.x; i < NF * (kPackS / 8); i += blockDim.x) {
+        const int f = i / (kPackS / 8), c = i % (kPackS / 8);
+        const int s = s0 + 8 * c, frame = ft * NF + f;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (frame < nf && s >= 0 && s < S)
+            v = __ldg(reinterpret_cast<const uint4*>(rf + ((size_t)frame * R + row) * S + s));
+        const uint16_t* h = reinterpret_cast<const uint16_t*>(&v);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) tile[8 * c + t][f] = h[t];
+    }
+    __syncthreads();
+    // store 64 sample rows of NF frames, 16-byte chunks swizzled
+    const int cpr = NF / 8;  // chunks per sample row
+    __half* dst = out + (((size_t)ft * R + row) * Sp + (size_t)sb * kPackS) * NF;
+    for (int i = threadIdx.x; i < kPackS * cpr; i += blockDim.x) {
+        const int k = i / cpr, c = i % cpr;
+        uint32_t w[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            w[t] = (uint32_t)tile[k][8 * c + 2 * t] | ((uint32_t)tile[k][8 * c + 2 * t + 1] << 16);
+        *reinterpret_cast<uint4*>(dst + (size_t)k * NF + 8 * mn_swizzle(c, k, NF)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Shared-memory descriptor of one MN-major K-step chunk (16 sample rows of NF
+// frames) in the swizzle matching NF (64: 128-byte, 32: 64-byte, 16: 32-byte):
+// a single swizzle atom spans the MN extent, atoms of 8 rows follow along K.
+// Both byte-offset fields carry the 8-row stride; with one atom along MN only
+// the K-direction stride is read.
+__device__ __forceinline__ uint64_t desc_mn_chunk(uint32_t smem_addr, int NF) {
+    const uint64_t stride = (uint64_t)(8 * NF * 2) >> 4;
+    const uint64_t layout = NF == 64 ? 2 : NF == 32 ? 4 : 6;
+    return (uint64_t)((smem_addr & 0x3FFFFu) >> 4) | (stride << 16) | (stride << 32) |
+           ((uint64_t)1 << 46) | (layout << 61);
+}
 
 // Place the 4 FP16 weights `v` (packed in 64 bits) at half offset o (0..7)
 // of a 32-byte span: lo / hi are the two 16-byte chunks.
@@ -67,8 +170,19 @@ __device__ __forceinline__ void place4(uint64_t v, int o, uint4& lo, uint4& hi) 
     }
 }
 
-// Per-(tile, angle, element) window: entry = k0 * 8 + ksteps (k0 may be
-// negative; ksteps 0 means no contributing pixel).  Per tile: element range.
+// Hand-off between group g's 128 builders and its MMA warp (160 threads):
+// a barrier that both sides wait on, once per pair, which also tells every
+// participant whether any of them has given up.  While the builders write
+// pair j + 1 the MMA warp issues pair j, so the two overlap.
+__device__ __forceinline__ bool group_bar(int grp, int stop) {
+    constexpr int kCount = 32 * 5;
+    return grp == 0 ? named_bar_or<2>(kCount, stop) : named_bar_or<3>(kCount, stop);
+}
+
+// Per-(tile, angle, element) window: entry = k0 + ksteps, k0 a multiple of 8
+// and ksteps in 0..4 (0: no contributing pixel, or a window wholly outside
+// the record, whose samples are all zero).  Per tile: the range of
+// contributing elements.
 __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __restrict__ tab,
                                     int2* __restrict__ range, int* __restrict__ bad) {
     const int NE = d.n_elem, A = d.n_angles;
@@ -97,9 +211,14 @@ __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __res
             const int c_lo = lo - 2, c_hi = hi + 3;
             const int k0 = (int)floorf((float)c_lo / 8.f) * 8;
             const int span = c_hi - k0 + 1;
-            const int steps = (span + 15) / 16;
-            if (steps > 4) atomicExch(bad, 1);
-            entry = k0 * 8 + min(steps, 4);
+            int steps = (span + dtc::kKC - 1) / dtc::kKC;
+            // the kernel keeps a 16-bit copy of the entry in shared memory
+            if (steps > dtc::kMaxSteps || k0 < -32760 || k0 > 32760) atomicExch(bad, 1);
+            steps = min(steps, dtc::kMaxSteps);
+            // a window that misses [0, n_samples) reads only zeros; any other
+            // one lies inside the packed record's zero margins
+            if (k0 + dtc::kKC * steps <= 0 || k0 >= d.n_samples) steps = 0;
+            entry = k0 + steps;
             atomicMin(&range[tile].x, n);
             atomicMax(&range[tile].y, n);
         }
@@ -107,65 +226,73 @@ __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __res
     }
 }
 
-__global__ void __launch_bounds__(320, 1)
-    das_tc_kernel(const __grid_constant__ CUtensorMap tmap, DasDev d, const int* __restrict__ tab,
-                  const int2* __restrict__ range, int tiles_x, int nf, int NF,
+__global__ void __launch_bounds__(dtc::kThreads, 2)
+    das_tc_kernel(const __half* __restrict__ packed, DasDev d, const int* __restrict__ tab,
+                  const int2* __restrict__ range, int tiles_x, int nf, int NF, int C,
                   float* __restrict__ img) {
     using namespace dtc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int RB = r_bytes(NF);
-    uint8_t* sW = base;
-    uint8_t* sR = base + kWStages * kWBytes;
-    uint64_t* full_r = (uint64_t*)(sR + kRStages * RB);
-    uint64_t* empty_r = full_r + kRStages;
-    uint64_t* full_w = empty_r + kRStages;
-    uint64_t* empty_w = full_w + kWStages;
-    uint64_t* done = empty_w + kWStages;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    const int CB = chunk_bytes(NF);
+    const int A = d.n_angles, NE = d.n_elem;
+    const int Sp = packed_len(d.n_samples);
+    uint8_t* sW = base;                                        // [kWTiles] weight tiles
+    uint8_t* sC = base + kWTiles * kWBytes;                    // [kGroups][C] chunks
+    // group g, pair slot p: full completes when the pair's chunks have landed,
+    // empty when the pair's MMAs have finished reading its chunks and tile
+    uint64_t* full = (uint64_t*)(sC + kGroups * C * CB);      // [kGroups][kPairSlots]
+    uint64_t* empty = full + kGroups * kPairSlots;             // [kGroups][kPairSlots]
+    uint64_t* done = empty + kGroups * kPairSlots;             // [kGroups]
+    uint32_t* tmem_slot = (uint32_t*)(done + kGroups);
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
-    int* prev = (int*)((uint8_t*)full_r + 1024);              // [kWStages][kM]
-    int2* s_base = (int2*)(prev + kWStages * kM);              // [A][kM]: transmit split
-    int* s_tab = (int*)(s_base + d.n_angles * kM);             // [pair]: window entries
+    int* s_used = (int*)(tmem_slot + 2);                       // [kGroups]
+    int8_t* prev = (int8_t*)((uint8_t*)full + 1024);           // [kWTiles][kM]
+    int2* s_base = (int2*)(prev + kWTiles * kM);               // [A][kM]: transmit split
+    int16_t* s_tab = (int16_t*)(s_base + A * kM);              // [pair]: window entries
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, tz = tile / tiles_x;
     const int f0 = blockIdx.y * NF;
-    const int A = d.n_angles, NE = d.n_elem;
     const int2 rg = range[tile];
     const int n_lo = rg.x, n_hi = rg.y;
     const int npairs = n_hi >= n_lo ? (n_hi - n_lo + 1) * A : 0;
-    const uint32_t tcols = NF <= 32 ? 32 : (NF <= 64 ? 64 : 128);
-    const uint32_t idesc = idesc_f16_f32(kM, NF);
-    const uint32_t rbytes = (uint32_t)(NF * kKW * 2);
+    const uint32_t acc_cols = NF < 32 ? 32 : NF;              // columns per accumulator
+    const uint32_t tcols = kGroups * acc_cols;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kRStages; ++s) {
-            mbar_init(&full_r[s], 1);
-            mbar_init(&empty_r[s], 1);
+        for (int s = 0; s < kGroups * kPairSlots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < kWStages; ++s) {
-            mbar_init(&full_w[s], 4);
-            mbar_init(&empty_w[s], 1);
+        for (int g = 0; g < kGroups; ++g) {
+            mbar_init(&done[g], 1);
+            s_used[g] = 0;
         }
-        mbar_init(done, 1);
         *s_abort = 0;
         fence_barrier_init();
-        prefetch_tensormap(&tmap);
     }
     // zero the weight tiles once; afterwards only written chunks are erased
-    for (int i = threadIdx.x; i < kWStages * kWBytes / 16; i += blockDim.x)
+    for (int i = threadIdx.x; i < kWTiles * kWBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(sW)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = threadIdx.x; i < kWStages * kM; i += blockDim.x) prev[i] = -1;
-    // this tile's window entries (pair order: element-major, angle-minor), so
-    // that no role waits on a global load per pair
+    for (int i = threadIdx.x; i < kWTiles * kM; i += blockDim.x) prev[i] = -1;
+    // this tile's window entries (pair order: element-major, angle-minor) and
+    // the transmit split of its pixels, so that no role waits on a global load
+    // per pair
     {
         const int* tt = tab + (size_t)tile * A * NE;
         for (int i = threadIdx.x; i < npairs; i += blockDim.x)
-            s_tab[i] = __ldg(tt + (i % A) * NE + n_lo + i / A);
+            s_tab[i] = (int16_t)__ldg(tt + (i % A) * NE + n_lo + i / A);
+        for (int i = threadIdx.x; i < A * kM; i += blockDim.x) {
+            const int a = i / kM, m = i % kM;
+            const int ix = tx * kTX + m % kTX, iz = tz * kTZ + m / kTX;
+            const int ixc = ix < d.nx ? ix : 0, izc = iz < d.nz ? iz : 0;
+            const int bi = __ldg(d.bxi + a * d.nx + ixc) + __ldg(d.bzi + a * d.nz + izc);
+            const float bf = __ldg(d.bxf + a * d.nx + ixc) + __ldg(d.bzf + a * d.nz + izc);
+            s_base[i] = make_int2(bi, __float_as_int(bf));
+        }
     }
-    if (warp == 1) {
+    if (warp == 0) {
         tmem_alloc(tmem_slot, tcols);
         tmem_relinquish();
     }
@@ -175,70 +302,118 @@ __global__ void __launch_bounds__(320, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0) {
-        // ------------------------------------------ channel windows by TMA
+    if (warp < kBuilderWarp0) {
+        // ------------------- producer of group g: the K-steps of its pairs
+        const int grp = warp;
         if (lane == 0) {
-            uint32_t st = 0, ph = 0;
-            for (int q = 0; q < npairs && !*s_abort; ++q) {
-                const int n = n_lo + q / A, a = q % A;
+            uint64_t* gfull = full + grp * kPairSlots;
+            uint64_t* gempty = empty + grp * kPairSlots;
+            uint8_t* ring = sC + grp * C * CB;
+            const __half* src_tile = packed + (size_t)blockIdx.y * A * NE * Sp * NF;
+            int head = 0, free_chunks = C, oldest = 0, j = 0;
+            int n = n_lo + grp / A, a = grp % A;
+            bool bad = false;
+            for (int q = grp; q < npairs && !bad; q += kGroups, ++j) {
                 const int e = s_tab[q];
-                if (!mbar_wait(&empty_r[st], ph ^ 1, &g_das_tc_wait_error, 301)) {
-                    *s_abort = 1;
-                    break;
-                }
-                mbar_arrive_expect_tx(&full_r[st], rbytes);
-                tma_load_3d(sR + st * RB, &tmap, &full_r[st], e >> 3, a * NE + n, f0);
-                if (++st == kRStages) { st = 0; ph ^= 1; }
-            }
-        }
-        __syncwarp();
-    } else if (warp == 1) {
-        // ------------------------------------------------------- MMAs
-        if (lane == 0) {
-            uint32_t rs = 0, rph = 0, ws = 0, wph = 0;
-            bool first = true;
-            for (int q = 0; q < npairs && !*s_abort; ++q) {
-                const int e = s_tab[q];
-                const bool ok = mbar_wait(&full_w[ws], wph, &g_das_tc_wait_error, 302) &&
-                                mbar_wait(&full_r[rs], rph, &g_das_tc_wait_error, 303);
-                if (!ok) {
-                    *s_abort = 1;
-                    break;
-                }
-                tc_fence_after();
                 const int steps = e & 7;
-                const uint32_t wa = smem_u32(sW + ws * kWBytes), ra = smem_u32(sR + rs * RB);
-                for (int kk = 0; kk < steps; ++kk) {
-                    mma_f16(tmem, desc_sw128_kmajor(wa) + 2 * kk, desc_sw128_kmajor(ra) + 2 * kk,
-                            idesc, first ? 0u : 1u);
-                    first = false;
+                // reuse of the pair slot, and room for this pair's chunks:
+                // retire the oldest pairs in flight
+                while (!bad && oldest < j && (oldest <= j - kPairSlots || free_chunks < steps)) {
+                    if (!mbar_wait_or_abort(&gempty[oldest % kPairSlots],
+                                            (uint32_t)(oldest / kPairSlots) & 1u, s_abort,
+                                            &g_das_tc_wait_error, 301)) {
+                        bad = true;
+                        break;
+                    }
+                    free_chunks += s_tab[grp + kGroups * oldest] & 7;
+                    ++oldest;
                 }
-                mma_commit(&empty_w[ws]);
-                mma_commit(&empty_r[rs]);
-                if (++ws == kWStages) { ws = 0; wph ^= 1; }
-                if (++rs == kRStages) { rs = 0; rph ^= 1; }
+                if (bad) break;
+                uint64_t* bar = &gfull[j % kPairSlots];
+                mbar_arrive_expect_tx(bar, (uint32_t)(steps * CB));
+                if (steps) {
+                    // sample rows k0 .. k0 + 16 steps of row (a, n): contiguous
+                    const uint8_t* src = reinterpret_cast<const uint8_t*>(
+                        src_tile + ((size_t)(a * NE + n) * Sp + (size_t)((e & ~7) + kPad)) * NF);
+                    const int first = steps <= C - head ? steps : C - head;
+                    bulk_load(ring + head * CB, src, (uint32_t)(first * CB), bar);
+                    if (first < steps)
+                        bulk_load(ring, src + (size_t)first * CB, (uint32_t)((steps - first) * CB),
+                                  bar);
+                }
+                head += steps;
+                if (head >= C) head -= C;
+                free_chunks -= steps;
+                a += kGroups;
+                while (a >= A) {
+                    a -= A;
+                    ++n;
+                }
             }
-            mma_commit(done);
+            if (*s_abort) {
+                // the consumers gave up: let the copies still in flight land
+                // before the CTA's shared memory is released
+                for (int k = 1; k <= kPairSlots && j - k >= oldest; ++k) {
+                    const int jj = j - k;
+                    mbar_wait(&gfull[jj % kPairSlots], (uint32_t)(jj / kPairSlots) & 1u,
+                              &g_das_tc_wait_error, 306);
+                }
+            }
         }
         __syncwarp();
+    } else if (warp >= kMmaWarp0) {
+        // ------------------------------------------ MMA warp of group g
+        const int grp = warp - kMmaWarp0;
+        const uint32_t acc = tmem + (uint32_t)grp * acc_cols;
+        const uint32_t idesc = idesc_f16_f32(kM, NF) | (1u << 16);  // B is MN-major
+        uint64_t* gfull = full + grp * kPairSlots;
+        uint64_t* gempty = empty + grp * kPairSlots;
+        const uint32_t ring = smem_u32(sC + grp * C * CB);
+        int pos = 0, j = 0;  // first chunk of pair j in the ring
+        bool first = true, bad = false;
+        for (int q = grp; q < npairs; q += kGroups, ++j) {
+            // the group's weight tile of pair q is written (leave together on an abort)
+            if (group_bar(grp, bad || *s_abort)) break;
+            const int steps = s_tab[q] & 7;
+            if (lane == 0) {
+                if (!bad && mbar_wait_or_abort(&gfull[j % kPairSlots],
+                                               (uint32_t)(j / kPairSlots) & 1u, s_abort,
+                                               &g_das_tc_wait_error, 303)) {
+                    tc_fence_after();
+                    const uint64_t wdesc =
+                        desc_sw128_kmajor(smem_u32(sW + (q & (kWTiles - 1)) * kWBytes));
+                    for (int kk = 0; kk < steps; ++kk) {
+                        int c = pos + kk;
+                        if (c >= C) c -= C;
+                        mma_f16(acc, wdesc + 2 * kk, desc_mn_chunk(ring + (uint32_t)(c * CB), NF),
+                                idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+                    mma_commit(&gempty[j % kPairSlots]);
+                } else {
+                    bad = true;
+                }
+            }
+            pos += steps;
+            if (pos >= C) pos -= C;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            s_used[grp] = first ? 0 : 1;
+            mma_commit(&done[grp]);  // arrives once this thread's MMAs have completed
+        }
+        __syncwarp();
+        named_bar_arrive<1>(kEpiBarCount);
     } else {
-        // ------------ weight tiles, one pixel per thread; two groups of four
-        // warps take alternate pairs (stages g and g + 2 of the ring)
-        const int grp = (warp - 2) >> 2;
+        // ------------------- weight tiles, one pixel per thread; group g takes
+        // pairs g, g + 2, ... into weight tiles g and g + 2
+        const int grp = (warp - kBuilderWarp0) >> 2;
         const int m = 32 * (warp & 3) + lane;  // tensor-memory lane = pixel row of W
-        const int col = m % kTX;
-        const int ix = tx * kTX + col, iz = tz * kTZ + m / kTX;
+        const int ix = tx * kTX + m % kTX, iz = tz * kTZ + m / kTX;
         const bool valid = ix < d.nx && iz < d.nz;
         const int ixc = valid ? ix : 0, izc = valid ? iz : 0;
         const float zs = __ldg(d.zs + izc);
-        if (grp == 0) {
-            for (int a = 0; a < A; ++a) {
-                const int bi = __ldg(d.bxi + a * d.nx + ixc) + __ldg(d.bzi + a * d.nz + izc);
-                const float bf = __ldg(d.bxf + a * d.nx + ixc) + __ldg(d.bzf + a * d.nz + izc);
-                s_base[a * kM + m] = make_int2(bi, __float_as_int(bf));
-            }
-        }
-        asm volatile("bar.sync 1, 256;" ::: "memory");  // both groups read s_base
+        uint64_t* gempty = empty + grp * kPairSlots;
         uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
         const int swz = m & 7;
         float w = 0.f, exc = 0.f;
@@ -248,109 +423,117 @@ __global__ void __launch_bounds__(320, 1)
         // (a single-angle plan gives each group every other element)
         int pre_n = n;
         float dxs_next = n <= n_hi ? __ldg(d.dxs + (size_t)n * d.nx + ixc) : 0.f;
-        for (int q = grp; q < npairs && !*s_abort; q += 2) {
+        bool bad = false;
+        int j = 0;
+        for (int q = grp; q < npairs; q += kGroups, ++j) {
             if (n != cur_n) {
                 cur_n = n;
                 const float dxs = n == pre_n ? dxs_next : __ldg(d.dxs + (size_t)n * d.nx + ixc);
-                pre_n = n + (A == 1 ? 2 : 1);
+                pre_n = n + (A == 1 ? kGroups : 1);
                 if (pre_n <= n_hi) dxs_next = __ldg(d.dxs + (size_t)pre_n * d.nx + ixc);
                 w = valid ? apod_weight(dxs, zs, d.fnum) : 0.f;
                 exc = rx_excess(dxs, zs);
             }
-            const int st = q & (kWStages - 1);
-            const uint32_t ph = (uint32_t)(q / kWStages) & 1u;
+            const int st = q & (kWTiles - 1);
             const int e = s_tab[q];
-            const int k0 = e >> 3, lim = (e & 7) * 16;
-            if (!mbar_wait(&empty_w[st], ph ^ 1u, &g_das_tc_wait_error, 304)) {
-                *s_abort = 1;
-                break;
-            }
-            uint8_t* W = rowp + st * kWBytes;
-            const int pc = prev[st * kM + m];
-            if (pc >= 0) {
-                *reinterpret_cast<uint4*>(W + ((((pc >> 3)) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
-                if ((pc & 7) > 4)
-                    *reinterpret_cast<uint4*>(W + ((((pc >> 3) + 1) ^ swz) << 4)) =
-                        make_uint4(0, 0, 0, 0);
-            }
-            int nc = -1;
-            if (w != 0.f) {
-                const int2 bs = s_base[a * kM + m];
-                const float uf = __int_as_float(bs.y) + exc;
-                const float fl = floorf(uf);
-                const float phi = uf - fl;
-                const int i = bs.x + (int)fl;
-                float v[4];
-                int c;
-                if (d.interp == TIDAS_INTERP_CUBIC) {
-                    keys_weights(phi, v[0], v[1], v[2], v[3]);
-                    c = i - 1 - k0;
-                } else {
-                    v[0] = 1.f - phi;
-                    v[1] = phi;
-                    v[2] = 0.f;
-                    v[3] = 0.f;
-                    c = i - k0;
+            const int k0 = e & ~7, steps = e & 7;
+            // the tile was last read by this group's pair j - 2
+            if (j >= 2)
+                bad = bad || !mbar_wait_or_abort(&gempty[(j - 2) % kPairSlots],
+                                                 (uint32_t)((j - 2) / kPairSlots) & 1u, s_abort,
+                                                 &g_das_tc_wait_error, 304);
+            if (!bad) {
+                uint8_t* W = rowp + st * kWBytes;
+                const int pc = prev[st * kM + m];
+                if (pc >= 0) {
+                    *reinterpret_cast<uint4*>(W + (((pc >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+                    if ((pc & 7) > 4)
+                        *reinterpret_cast<uint4*>(W + ((((pc >> 3) + 1) ^ swz) << 4)) =
+                            make_uint4(0, 0, 0, 0);
                 }
-                if (c >= 0 && c + 3 < lim) {  // always true by the table's construction
-                    const __half2 h01 = __floats2half2_rn(w * v[0], w * v[1]);
-                    const __half2 h23 = __floats2half2_rn(w * v[2], w * v[3]);
-                    const uint64_t pk = (uint64_t)*reinterpret_cast<const uint32_t*>(&h01) |
-                                        ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
-                    uint4 lo, hi;
-                    place4(pk, c & 7, lo, hi);
-                    *reinterpret_cast<uint4*>(W + (((c >> 3) ^ swz) << 4)) = lo;
-                    if ((c & 7) > 4) *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
-                    nc = c;
+                int nc = -1;
+                if (w != 0.f) {
+                    const int2 bs = s_base[a * kM + m];
+                    const float uf = __int_as_float(bs.y) + exc;
+                    const float fl = floorf(uf);
+                    const float phi = uf - fl;
+                    const int i = bs.x + (int)fl;
+                    float v[4];
+                    int c;
+                    if (d.interp == TIDAS_INTERP_CUBIC) {
+                        keys_weights(phi, v[0], v[1], v[2], v[3]);
+                        c = i - 1 - k0;
+                    } else {
+                        v[0] = 1.f - phi;
+                        v[1] = phi;
+                        v[2] = 0.f;
+                        v[3] = 0.f;
+                        c = i - k0;
+                    }
+                    // inside the window by the table's construction, unless the
+                    // window misses the record (steps 0)
+                    if (c >= 0 && c + 3 < steps * kKC) {
+                        const __half2 h01 = __floats2half2_rn(w * v[0], w * v[1]);
+                        const __half2 h23 = __floats2half2_rn(w * v[2], w * v[3]);
+                        const uint64_t pk = (uint64_t)*reinterpret_cast<const uint32_t*>(&h01) |
+                                            ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
+                        uint4 lo, hi;
+                        place4(pk, c & 7, lo, hi);
+                        *reinterpret_cast<uint4*>(W + (((c >> 3) ^ swz) << 4)) = lo;
+                        if ((c & 7) > 4)
+                            *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
+                        nc = c;
+                    }
                 }
+                prev[st * kM + m] = (int8_t)nc;
             }
-            prev[st * kM + m] = nc;
             fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&full_w[st]);
-            a += 2;
+            if (group_bar(grp, bad || *s_abort)) break;
+            a += kGroups;
             while (a >= A) {
                 a -= A;
                 ++n;
             }
         }
-        if (grp == 0) {  // epilogue: the first group holds every tensor-memory lane
-        // --------------------------------------------------- epilogue
-        bool have = npairs > 0;
-        if (have && !mbar_wait(done, 0, &g_das_tc_wait_error, 305)) {
-            *s_abort = 1;
-            have = false;
-        }
+        named_bar_sync<1>(kEpiBarCount);  // the MMA warps have committed `done`
+        // --------------------------------------------------- epilogue: group g
+        // drains the 32-column chunks j = g, g + 2, ... of both accumulators.
+        // The waits are not cut short by an abort: MMAs still in flight must
+        // finish before tensor memory is released.
+        bool ok = true;
+        for (int g = 0; g < kGroups; ++g)
+            ok = mbar_wait(&done[g], 0, &g_das_tc_wait_error, 305) && ok;
+        ok = ok && !*s_abort;
         tc_fence_after();
         const size_t plane = (size_t)d.nz * d.nx;
-        for (int j = 0; j < NF; j += 32) {
-            uint32_t r[32];
-            if (have && !*s_abort) {
-                tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)j, r);
-                tmem_ld_wait();
-            } else {
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        for (int jc = 32 * grp; jc < NF; jc += 32 * kGroups) {
+            float sum[32];
 #pragma unroll
-                for (int e2 = 0; e2 < 32; ++e2) r[e2] = 0u;
+            for (int e2 = 0; e2 < 32; ++e2) sum[e2] = 0.f;
+            for (int g = 0; g < kGroups; ++g) {
+                if (!ok || !s_used[g]) continue;
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)g * acc_cols + (uint32_t)jc, r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int e2 = 0; e2 < 32; ++e2) sum[e2] += __uint_as_float(r[e2]);
             }
             if (valid) {
-                float* dst = img + (size_t)(f0 + j) * plane + (size_t)iz * d.nx + ix;
+                float* dst = img + (size_t)(f0 + jc) * plane + (size_t)iz * d.nx + ix;
 #pragma unroll
                 for (int e2 = 0; e2 < 32; ++e2)
-                    if (f0 + j + e2 < nf && j + e2 < NF) dst[(size_t)e2 * plane] = __uint_as_float(r[e2]);
+                    if (f0 + jc + e2 < nf && jc + e2 < NF) dst[(size_t)e2 * plane] = sum[e2];
             }
-        }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, tcols);
     }
 }
-
-int make_map_3d(CUtensorMap* map, const void* ptr, CUtensorMapDataType dt, int esize, int nz,
-                int nx, int nf, int box_x, int box_f, CUtensorMapSwizzle sw);
 
 // Build the window table of an FP16 plan (once, at plan creation).
 int das_tc_prepare(Plan& P) {
@@ -374,30 +557,52 @@ int das_tc_prepare(Plan& P) {
     if (rc) return rc;
     int bad = 0;
     TIDAS_CUDA(cudaMemcpy(&bad, d_bad, 4, cudaMemcpyDeviceToHost));
-    P.tc_ok = (bad == 0) && dtc::smem_bytes(16, d.n_angles, d.n_elem) <= 227 * 1024;
+    P.tc_ok = (bad == 0) &&
+              dtc::smem_bytes(16, dtc::kMinChunks, d.n_angles, d.n_elem) <= dtc::kSmemMax;
     return TIDAS_OK;
 }
 
 int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st) {
     using namespace dtc;
     const DasDev& d = P.dev;
-    // the widest frame tile (MMA N) that the batch fills and shared memory holds
-    int NF = 16;
-    for (int c = 128; c > 16; c /= 2)
-        if (nf >= c && smem_bytes(c, d.n_angles, d.n_elem) <= 227 * 1024) {
-            NF = c;
-            break;
+    const int A = d.n_angles, NE = d.n_elem, R = A * NE;
+    // The widest frame tile (MMA N) up to 64 that the batch fills, preferring
+    // one that leaves room for two CTAs per SM; then as many chunks per group
+    // ring as the same budget holds.
+    int NF = 0;
+    size_t budget = kSmemTwoPerSM;
+    for (int pass = 0; pass < 2 && !NF; ++pass) {
+        budget = pass == 0 ? kSmemTwoPerSM : kSmemMax;
+        for (int c = 64; c >= 16 && !NF; c /= 2)
+            if ((nf >= c || c == 16) && smem_bytes(c, kMinChunks, A, NE) <= budget) NF = c;
+    }
+    if (!NF) return set_error(TIDAS_ERR_UNSUPPORTED, "das_tc: tables exceed shared memory");
+    int C = kMinChunks;
+    while (C < kMaxChunks && smem_bytes(NF, C + 1, A, NE) <= budget) ++C;
+    // the plan's staging buffer for the repacked batch (grown on demand)
+    const int Sp = packed_len(d.n_samples);
+    const int FT = (nf + NF - 1) / NF;
+    const size_t need = (size_t)FT * R * Sp * NF * 2;
+    {
+        std::lock_guard<std::mutex> lock(P.tc_ws_mutex);
+        if (need > P.tc_ws_bytes) {
+            if (P.tc_ws) TIDAS_CUDA(cudaFree(P.tc_ws));
+            P.tc_ws = nullptr;
+            P.tc_ws_bytes = 0;
+            TIDAS_CUDA(cudaMalloc(&P.tc_ws, need));
+            P.tc_ws_bytes = need;
         }
-    CUtensorMap map;
-    // channel data as [frames][angles * elements][samples]: box 64 samples x 1 row x NF frames
-    int rc = make_map_3d(&map, rf, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, d.n_angles * d.n_elem,
-                         d.n_samples, nf, kKW, NF, CU_TENSOR_MAP_SWIZZLE_128B);
+    }
+    __half* packed = (__half*)P.tc_ws;
+    das_tc_pack_kernel<<<(unsigned)((size_t)FT * R * (Sp / kPackS)), 256, 0, st>>>(
+        (const __half*)rf, packed, nf, R, d.n_samples, Sp, NF);
+    int rc = check_launch("das_tc_pack_kernel");
     if (rc) return rc;
-    const size_t smem = smem_bytes(NF, d.n_angles, d.n_elem);
+    const size_t smem = smem_bytes(NF, C, A, NE);
     cudaFuncSetAttribute(das_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(P.tc_tiles, (nf + NF - 1) / NF);
-    das_tc_kernel<<<grid, 320, smem, st>>>(map, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF,
-                                           img);
+    dim3 grid(P.tc_tiles, FT);
+    das_tc_kernel<<<grid, kThreads, smem, st>>>(packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf,
+                                                NF, C, img);
     return check_launch("das_tc_kernel");
 }
 

@@ -272,6 +272,10 @@ extern "C" int das_plan_destroy(das_plan plan) {
         cudaError_t e3 = cudaFree(P->tc_tab);
         if (e2 == cudaSuccess) e2 = e3;
     }
+    if (P->tc_ws) {
+        cudaError_t e4 = cudaFree(P->tc_ws);
+        if (e2 == cudaSuccess) e2 = e4;
+    }
     delete P;
     if (e != cudaSuccess) return check_cuda(e, "cudaDeviceSynchronize(plan destroy)");
     return check_cuda(e2, "cudaFree(plan tables)");

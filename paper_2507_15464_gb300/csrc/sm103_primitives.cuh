@@ -46,6 +46,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Same, suspending the thread until the phase completes or `hint_ns`
+// nanoseconds pass (instead of the short system-defined limit), so that a
+// waiting warp does not spin on the issue slots of its sub-partition.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint32_t kWaitSleepNs = 20000;
+
 // Wait for the phase with the given parity to complete, for at most
 // `limit_ns` nanoseconds of wall time.  On timeout record `code` in *flag and
 // return false; the caller then abandons its work.
@@ -54,13 +71,58 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* f
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
-        for (int i = 0; i < 64; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
         if (globaltimer() - t0 > limit_ns) {
             atomicExch(flag, code);
             return false;
         }
     }
+}
+
+// Same contract as mbar_wait, and give up at once when another role of the
+// CTA has raised *abort (after its own wait ran out); a timeout here raises it.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   volatile int* abort, int* flag, int code,
+                                                   uint64_t limit_ns = 1000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (*abort) return false;
+        if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
+        if (globaltimer() - t0 > limit_ns) {
+            atomicExch(flag, code);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// Named barrier ID over `count` threads (a multiple of 32).  The ID is a
+// compile-time constant so that the kernel reserves only the barriers it uses.
+template <int ID>
+__device__ __forceinline__ void named_bar_sync(int count) {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(count) : "memory");
+}
+// Arrive on named barrier ID without waiting (producer side of a hand-off
+// whose consumer waits with named_bar_sync on the same ID and count).
+template <int ID>
+__device__ __forceinline__ void named_bar_arrive(int count) {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "r"(count) : "memory");
+}
+// Named barrier that also returns, to every participant, whether any of them
+// passed a non-zero `pred` (a uniform decision, e.g. to leave a loop together).
+template <int ID>
+__device__ __forceinline__ bool named_bar_or(int count, int pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred), "n"(ID), "r"(count)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
@@ -98,6 +160,16 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(smem_dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+// contiguous global -> shared copy of `bytes` (multiple of 16; both addresses
+// 16-byte aligned), completing on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
 // shared -> global tensor store of one box; completion tracked by bulk groups
@@ -197,6 +269,13 @@ __device__ __forceinline__ void tmem_ld_wait() {
 __device__ __forceinline__ uint64_t desc_sw128_kmajor(uint32_t smem_addr) {
     return (uint64_t)((smem_addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
            ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Same for a K-major tile stored with the 32-byte swizzle: rows of 16 16-bit
+// elements (one K-step), 8-row groups 256 bytes apart, layout type 6.  The
+// tile base must be 256-byte aligned.
+__device__ __forceinline__ uint64_t desc_sw32_kmajor(uint32_t smem_addr) {
+    return (uint64_t)((smem_addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
 
 // Instruction descriptor of kind::f16 with FP32 accumulation, BF16 A and B,
