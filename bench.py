@@ -214,23 +214,28 @@ def run_ours(args):
     clocks = clk.summary()
     value = BATCH * npx * world / (ms * 1e-3) / 1e6
 
-    # ---- roofline of das_forward_kernel (the only launch of a step)
+    # ---- roofline of the step's dominant kernel, das_tc_kernel.  A step is two
+    # launches inside one das_forward call: das_tc_pack_kernel (repacks the
+    # batch, ~7 % of the step) and das_tc_kernel.  They cannot be timed apart
+    # through the C ABI, so "achieved" divides by the whole step's event time
+    # (a lower bound for the kernel itself).
     updates = active_updates(g) * BATCH
     flops = updates * 10.0  # cubic: 4 tap MACs + 1 apodization MAC per update
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     fp32_peak = sms * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s at the maximum SM clock
     alg_bytes = rf.numel() * 2 + img.numel() * 4
-    # DRAM bytes of one launch of the timed kernel, from the ncu capture summarised
-    # in profiles/das_tc_kernel_pw128_compound_64frames_f16.md (same kernel, same
-    # 64-frame launch); None whenever the kernel changes after that capture
-    traffic = 950.2e6 if BATCH == 64 else None
+    # DRAM bytes of one das_tc_kernel launch (64 frames), from the ncu capture
+    # summarised in profiles/das_tc_kernel_pw128_compound_64frames_f16.md;
+    # None whenever the kernel changes after that capture
+    traffic = 691.8e6 if BATCH == 64 else None
     roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
             "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
             "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x 2070 MHz" % sms,
             "work": "%.4g updates x 10 flop (cubic taps + apodization)" % updates,
-            "note": "tensor-core kernel limited by the issue rate of its weight-building "
-                    "warps; tensor pipe 16.7 % busy (ncu)"}
+            "timed": "whole step (das_tc_pack_kernel + das_tc_kernel)",
+            "note": "issue-bound: the weight-building warps keep 69 % of issue slots busy; "
+                    "tensor pipe 4.4 % busy (ncu)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     hbm = {"achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
            "peak_source": peak_src, "bytes_per_launch": alg_bytes}
@@ -315,7 +320,7 @@ def run_ours(args):
                    "parallelism": "frames sharded across ranks, no collective",
                    "l2": "inputs larger than L2 (738 MB per step)"},
         "roofline": roof, "hbm": hbm, "clocks": clocks, "e2e": e2e,
-        "gpu_launches": args.steps, "cpu_baseline": cpu,
+        "gpu_launches": 2 * args.steps, "cpu_baseline": cpu,
     }
     line.update(extra)
     if rank == 0:
