@@ -51,7 +51,7 @@ def _variants():
 
 @pytest.mark.parametrize("variant", _variants())
 @pytest.mark.parametrize("shape", [(3, 40, 512, 63), (5, 17, 200, 31), (2, 9, 64, 4),
-                                   (1, 3, 24, 1)])
+                                   (1, 3, 24, 1), (6, 5, 1500, 63), (9, 4, 96, 100)])
 def test_tidas_forward_matches_oracle(variant, shape):
     import oracle
     nf, nz, nx, taps = shape
