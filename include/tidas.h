@@ -237,7 +237,7 @@ int tidas_psf_batch(das_plan plan, const double* samples, int32_t n, int32_t tap
                     int32_t ldo, float* norm, void* stream);
 
 /* out[i] = sum of the receive apodization weights at (x, z) for F#
- * (samples as tidas_psf_batch; the kernel scale). */
+ * (samples as tidas_psf_batch; the kernel scale).  Evaluated in FP32. */
 int tidas_apod_sum(das_plan plan, const double* samples, int64_t n, float* out, void* stream);
 
 /* C[M x N] = act(A[M x K] * B[N x K]^T + bias[N]) on tcgen05 tensor cores.
@@ -279,7 +279,7 @@ int tidas_mse(const float* pred, const float* target, int32_t rows, int32_t cols
 
 /* Network inputs: out16[i][0..63] = BF16(2 (s_ic - lo[c]) / (hi[c] - lo[c]) - 1)
  * for the 4 features of samples [n][4], zeros in columns 4..63.  lo4 / hi4
- * are DEVICE float[4]. */
+ * are DEVICE float[4]; out16 is 16-byte aligned. */
 int tidas_encode(const double* samples, int32_t n, const float* lo4, const float* hi4, void* out16,
                  void* stream);
 

@@ -295,16 +295,25 @@ __global__ void sum_partials_kernel(const double* __restrict__ p, int np, double
 }
 
 // features (x, z, fnum, angle) -> [-1, 1] inputs, BF16, padded to 64 columns
+// Eight threads per row, one 16-byte chunk of 8 BF16 each (coalesced rows).
 __global__ void encode_kernel(const double* __restrict__ samples, int n, const float* __restrict__ lo,
                               const float* __restrict__ hi, __nv_bfloat16* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = t >> 3;
+    const int c = (int)(t & 7);
     if (i >= n) return;
-    __nv_bfloat16* o = out + (size_t)i * 64;
-    for (int c = 0; c < 64; ++c) {
-        float v = 0.f;
-        if (c < 4) v = 2.f * ((float)samples[(size_t)i * 4 + c] - lo[c]) / (hi[c] - lo[c]) - 1.f;
-        o[c] = __float2bfloat16_rn(v);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (c == 0) {
+        float f[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            f[k] = 2.f * ((float)samples[i * 4 + k] - lo[k]) / (hi[k] - lo[k]) - 1.f;
+        const __nv_bfloat162 a = __floats2bfloat162_rn(f[0], f[1]);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(f[2], f[3]);
+        v.x = *reinterpret_cast<const uint32_t*>(&a);
+        v.y = *reinterpret_cast<const uint32_t*>(&b);
     }
+    reinterpret_cast<uint4*>(out + i * 64)[c] = v;
 }
 
 }  // namespace tidas
@@ -463,14 +472,29 @@ __global__ void row_scale_kernel(const float* __restrict__ in, int ldi, const fl
 }
 
 // sum of apodization weights at (x, z) for receive f-number F# (the kernel scale)
+// FP32: the sum only rescales the network's kernels (relative error ~1e-6
+// against FP64, far below the kernels' own error).
 __global__ void apod_sum_kernel(PsfArgs A, const double* __restrict__ samples, long long n,
                                 float* __restrict__ s) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double acc = 0.0;
-    for (int e = 0; e < A.n_elem; ++e)
-        acc += psf_apod(A, e, samples[4 * i], samples[4 * i + 1], samples[4 * i + 2]);
-    s[i] = (float)acc;
+    const float x = (float)samples[4 * i], z = (float)samples[4 * i + 1];
+    const float fnum = (float)samples[4 * i + 2];
+    if (fnum <= 0.f) {
+        s[i] = (float)A.n_elem;
+        return;
+    }
+    const float pitch = (float)A.pitch, mid = 0.5f * (float)(A.n_elem - 1);
+    const float k = fnum / z;
+    float acc = 0.f;
+    for (int e = 0; e < A.n_elem; ++e) {
+        const float r = (x - ((float)e - mid) * pitch) * k;
+        if (fabsf(r) <= 0.5f) {
+            const float cw = cospif(r);
+            acc = fmaf(cw, cw, acc);
+        }
+    }
+    s[i] = acc;
 }
 
 static PsfArgs psf_args(const Plan& P, int taps) {
@@ -601,8 +625,9 @@ extern "C" int tidas_mse(const float* pred, const float* target, int32_t rows, i
 extern "C" int tidas_encode(const double* samples, int32_t n, const float* lo4, const float* hi4,
                             void* out16, void* stream) {
     TIDAS_REQUIRE(samples && lo4 && hi4 && out16 && n >= 1, "tidas_encode: bad arguments");
-    encode_kernel<<<(n + 255) / 256, 256, 0, ST(stream)>>>(samples, n, lo4, hi4,
-                                                           (__nv_bfloat16*)out16);
+    TIDAS_REQUIRE(((uintptr_t)out16 % 16) == 0, "tidas_encode: out16 must be 16-byte aligned");
+    encode_kernel<<<(unsigned)(((long long)n * 8 + 255) / 256), 256, 0, ST(stream)>>>(
+        samples, n, lo4, hi4, (__nv_bfloat16*)out16);
     return check_launch("encode_kernel");
 }
 

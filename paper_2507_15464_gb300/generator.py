@@ -117,11 +117,12 @@ class KernelMLP:
                   _ptr(c16) if c16 is not None else None, ldc, _stream())
 
     def forward_into(self, x16, M, h32, h16, y32):
-        """Forward pass of M encoded rows: hidden activations (FP32 + BF16) and
-        the FP32 output [M, 64]."""
+        """Forward pass of M encoded rows: hidden activations (BF16, and FP32
+        when h32 is given, for training) and the FP32 output [M, 64]."""
         a = x16
         for l in range(3):
-            self.gemm(a, self.W16[l], M, HID, a.shape[1], self.b[l], True, h32[l], h16[l], HID)
+            self.gemm(a, self.W16[l], M, HID, a.shape[1], self.b[l], True,
+                      h32[l] if h32 is not None else None, h16[l], HID)
             a = h16[l]
         self.gemm(a, self.W16[3], M, OUT, HID, self.b[3], False, y32, None, OUT)
 
@@ -198,13 +199,11 @@ class KernelMLP:
         capi.call("tidas_apod_sum", plan.handle, _ptr(samples), n, _ptr(scale), _stream())
         c = min(chunk, n)
         x16 = _bf16((c, IN))
-        h32 = [_f32((c, HID)) for _ in range(3)]
         h16 = [_bf16((c, HID)) for _ in range(3)]
         for s0 in range(0, n, chunk):
             m = min(chunk, n - s0)
             self.encode(samples[s0:s0 + m], x16[:m])
-            self.forward_into(x16[:m], m, [h[:m] for h in h32], [h[:m] for h in h16],
-                              out[s0:s0 + m])
+            self.forward_into(x16[:m], m, None, [h[:m] for h in h16], out[s0:s0 + m])
         capi.call("tidas_row_scale", _ptr(out), OUT, _ptr(scale), n, TAPS, _ptr(out), OUT,
                   _stream())
         return out

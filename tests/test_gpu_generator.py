@@ -49,6 +49,36 @@ def test_gemm_bf16_matches_fp64(M, N, K, bias, relu):
     assert rel_l2(host(c16), ref) <= 4e-3
 
 
+def test_apod_sum_and_encode_match_oracle():
+    # the inference scale (sum of Hann weights, FP32) and the network inputs
+    import oracle
+    from paper_2507_15464_gb300 import capi, ops
+    from paper_2507_15464_gb300.ops import _ptr, _stream
+    g = G()
+    base = presets.geometry("pw128_compound")
+    plan = ops.DasPlan(base)
+    u = generators.uniform((301, 4), 0.0, 1.0, (63,), np.float64)
+    lo, hi = np.array(g.BOUNDS_LO), np.array(g.BOUNDS_HI)
+    s = lo + u * (hi - lo)
+    s[:, 2] = np.array([1.0, 1.7, 3.0])[np.arange(301) % 3]
+    sd = torch.from_numpy(s).cuda()
+    out = torch.empty(301, device="cuda")
+    capi.call("tidas_apod_sum", plan.handle, _ptr(sd), 301, _ptr(out), _stream())
+    ref = np.empty(301)
+    for fn in (1.0, 1.7, 3.0):
+        O = oracle.Oracle(dict(base, fnum=fn))
+        for i in np.nonzero(s[:, 2] == fn)[0]:
+            ref[i] = sum(O.apod(n, s[i, 0], s[i, 1]) for n in range(base["n_elem"]))
+    assert rel_l2(host(out), ref) <= 1e-5
+    net = g.KernelMLP()
+    x16 = torch.empty((301, 64), dtype=torch.bfloat16, device="cuda")
+    net.encode(sd, x16)
+    enc = host(x16)
+    want = 2 * (s - lo) / (hi - lo) - 1
+    assert np.abs(enc[:, :4] - want).max() <= 2 ** -8
+    assert not enc[:, 4:].any()
+
+
 def _oracle_psf(xs, z, fnum, deg, taps=63):
     import oracle
     base = presets.geometry("pw128_compound")
