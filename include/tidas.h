@@ -283,6 +283,20 @@ int tidas_mse(const float* pred, const float* target, int32_t rows, int32_t cols
 int tidas_encode(const double* samples, int32_t n, const float* lo4, const float* hi4, void* out16,
                  void* stream);
 
+/* Fused inference of the kernel generator (the 4-layer MLP above), no
+ * hidden activations in global memory:
+ *   out[i][0..63] = scale[i] * (W4 relu(W3 relu(W2 relu(W1 x_i + b1) + b2) + b3) + b4)
+ * with x_i the encoding of samples[i] (as tidas_encode; lo4 / hi4 are HOST
+ * float[4] here), BF16 operands and activations, FP32 accumulation.
+ *   w16  HOST array of 4 DEVICE pointers to the BF16 weights, row-major
+ *        [out][in]: W1 [256][64], W2 [256][256], W3 [256][256], W4 [64][256]
+ *   bias HOST array of 4 DEVICE pointers: b1, b2, b3 [256], b4 [64] float32
+ *   scale DEVICE float[n] or NULL (all ones); out [n][ldo] float32,
+ *   ldo >= 64 and a multiple of 4, 16-byte aligned. */
+int tidas_mlp_infer(const double* samples, int64_t n, const float* lo4, const float* hi4,
+                    const void* const* w16, const float* const* bias, const float* scale,
+                    float* out, int32_t ldo, void* stream);
+
 /* Eq. (2.13) with a kernel per pixel: img[f][z][x] = sum_t h[z][x][t] *
  * refl[f][z][x - t + taps/2]; kernels [nz * nx][ld], taps <= 64. */
 int tidas_forward_varying(const float* kernels, int32_t ld, int32_t taps, int32_t nz, int32_t nx,

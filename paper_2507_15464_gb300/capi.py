@@ -67,6 +67,7 @@ _SIG = {
                    ctypes.c_float, ctypes.c_float, _I, _P, _P, _P],
     "tidas_mse": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
     "tidas_encode": [_P, _I, _P, _P, _P, _P],
+    "tidas_mlp_infer": [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _I, _P],
     "tidas_forward_varying": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
     "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
     "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],

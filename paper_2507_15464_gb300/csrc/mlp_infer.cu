@@ -1,0 +1,300 @@
+// Fused inference of the learned tiDAS kernel generator on tcgen05: all four
+// layers of the 4 -> 256 -> 256 -> 256 -> 63 MLP for a tile of 128 samples,
+// without writing hidden activations to global memory.
+//
+// Persistent: one CTA per SM walks 128-row tiles.  Per tile the epilogue
+// warps encode the samples into the first layer's operand, and after each
+// layer read the FP32 accumulator from tensor memory, add the bias, apply
+// ReLU and write the BF16 activations back into shared memory (128-byte
+// swizzled, K-major: the next layer's A operand).  The weights, identical for
+// every tile, stream from L2 by TMA in 64-column chunks through a ring that
+// runs across layers and tiles.  Roles: warp 0 loads weights (and owns tensor
+// memory), warp 1 issues the MMAs, warps 2-5 run encode and epilogues (one
+// accumulator row per thread).  The last layer's output is scaled per row
+// (the apodization sum) and stored in FP32.
+#include "common.cuh"
+#include "sm103_primitives.cuh"
+
+namespace tidas {
+using namespace sm103;
+
+__device__ int g_mlp_infer_wait_error = 0;
+
+int read_clear_mlp_infer_wait_flag(int* v) {
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_mlp_infer_wait_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_mlp_infer_wait_error, &zero, sizeof(int));
+    return check_cuda(e, "mlp infer wait flag");
+}
+
+namespace mi {
+constexpr int kM = 128;       // samples per tile (UMMA M)
+constexpr int kHid = 256;
+constexpr int kIO = 64;       // padded input / output width
+constexpr int kKC = 64;       // K columns per weight chunk / activation chunk
+constexpr int kStages = 3;    // weight chunks in flight
+constexpr int kWBytes = kHid * kKC * 2;   // 32 KB (largest chunk)
+constexpr int kABytes = kM * kKC * 2;     // 16 KB per activation chunk
+constexpr int kAChunks = kHid / kKC;      // 4
+constexpr int kChunksPerTile = 1 + 3 * kAChunks;  // W1, W2 x4, W3 x4, W4 x4
+constexpr int kBias = 3 * kHid + kIO;
+constexpr size_t kSmem = 1024 + (size_t)kStages * kWBytes + (size_t)kAChunks * kABytes + 1024 +
+                         (size_t)kBias * 4;
+// weight chunk q of a tile: layer and K offset
+__host__ __device__ constexpr int chunk_layer(int q) { return q == 0 ? 0 : 1 + (q - 1) / kAChunks; }
+__host__ __device__ constexpr int chunk_k(int q) { return q == 0 ? 0 : ((q - 1) % kAChunks) * kKC; }
+}  // namespace mi
+
+struct MlpInferArgs {
+    float lo[4], hi[4];
+};
+
+__global__ void __launch_bounds__(192, 1)
+    mlp_infer_kernel(const __grid_constant__ CUtensorMap w1, const __grid_constant__ CUtensorMap w2,
+                     const __grid_constant__ CUtensorMap w3, const __grid_constant__ CUtensorMap w4,
+                     const float* __restrict__ b1, const float* __restrict__ b2,
+                     const float* __restrict__ b3, const float* __restrict__ b4,
+                     const double* __restrict__ samples, int n, MlpInferArgs enc,
+                     const float* __restrict__ scale, float* __restrict__ out, int ldo) {
+    using namespace mi;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sW = base;                                  // [kStages] weight chunks
+    uint8_t* sA = sW + kStages * kWBytes;                // [kAChunks] activation chunks
+    uint64_t* full = (uint64_t*)(sA + kAChunks * kABytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* a_full = empty + kStages;   // epilogue -> MMA: operand written, accumulator read
+    uint64_t* acc_full = a_full + 1;      // MMA -> epilogue: layer done
+    uint64_t* done = acc_full + 1;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* s_abort = (volatile int*)(tmem_slot + 1);
+    float* s_bias = (float*)((uint8_t*)full + 1024);     // b1 | b2 | b3 | b4
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (n + kM - 1) / kM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(a_full, 4);
+        mbar_init(acc_full, 1);
+        mbar_init(done, 1);
+        *s_abort = 0;
+        fence_barrier_init();
+        prefetch_tensormap(&w1);
+        prefetch_tensormap(&w2);
+        prefetch_tensormap(&w3);
+        prefetch_tensormap(&w4);
+    }
+    for (int i = threadIdx.x; i < kBias; i += blockDim.x)
+        s_bias[i] = i < kHid ? b1[i] : i < 2 * kHid ? b2[i - kHid] : i < 3 * kHid ? b3[i - 2 * kHid]
+                                                                              : b4[i - 3 * kHid];
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, kHid);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ weight chunks by TMA
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            for (int t = blockIdx.x; t < ntiles && !*s_abort; t += gridDim.x) {
+                for (int q = 0; q < kChunksPerTile; ++q) {
+                    if (!mbar_wait_or_abort(&empty[st], ph ^ 1u, s_abort, &g_mlp_infer_wait_error, 401))
+                        break;
+                    const int l = chunk_layer(q);
+                    const CUtensorMap* map = l == 0 ? &w1 : l == 1 ? &w2 : l == 2 ? &w3 : &w4;
+                    const uint32_t bytes = (l == 3 ? kIO : kHid) * kKC * 2;
+                    mbar_arrive_expect_tx(&full[st], bytes);
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(sW + st * kWBytes)),
+                        "l"(reinterpret_cast<uint64_t>(map)), "r"(chunk_k(q)), "r"(0),
+                        "r"(smem_u32(&full[st]))
+                        : "memory");
+                    if (++st == kStages) { st = 0; ph ^= 1; }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------- MMAs
+        if (lane == 0) {
+            const uint32_t id_h = idesc_bf16_f32(kM, kHid), id_o = idesc_bf16_f32(kM, kIO);
+            uint32_t st = 0, ph = 0, aph = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int q = 0;
+                for (int l = 0; l < 4 && ok; ++l) {
+                    ok = mbar_wait_or_abort(a_full, aph, s_abort, &g_mlp_infer_wait_error, 402);
+                    aph ^= 1u;
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int nchunks = l == 0 ? 1 : kAChunks;
+                    for (int c = 0; c < nchunks; ++c, ++q) {
+                        ok = mbar_wait_or_abort(&full[st], ph, s_abort, &g_mlp_infer_wait_error, 403);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t a = smem_u32(sA + c * kABytes), b = smem_u32(sW + st * kWBytes);
+#pragma unroll
+                        for (int kk = 0; kk < kKC / 16; ++kk)
+                            mma_f16(tmem, desc_sw128_kmajor(a) + 2 * kk, desc_sw128_kmajor(b) + 2 * kk,
+                                    l == 3 ? id_o : id_h, (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(&empty[st]);
+                        if (++st == kStages) { st = 0; ph ^= 1; }
+                    }
+                    mma_commit(acc_full);
+                }
+            }
+            mma_commit(done);
+            mbar_wait(done, 0, &g_mlp_infer_wait_error, 404);  // MMAs in flight end before dealloc
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------ encode and epilogues, one row each
+        const int q4 = warp & 3;                          // tensor-memory lane quadrant
+        const int r = 32 * q4 + lane;                     // row of the tile
+        const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
+        uint8_t* const arow = sA + (r >> 3) * 1024 + (r & 7) * 128;  // row in each chunk
+        const int swz = r & 7;
+        uint32_t cph = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int row = t * kM + r;
+            // encode: four features in [-1, 1], zeros in columns 4..63
+            {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (row < n) {
+                    float f[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        f[k] = 2.f * ((float)samples[(size_t)row * 4 + k] - enc.lo[k]) /
+                                   (enc.hi[k] - enc.lo[k]) - 1.f;
+                    const __nv_bfloat162 p0 = __floats2bfloat162_rn(f[0], f[1]);
+                    const __nv_bfloat162 p1 = __floats2bfloat162_rn(f[2], f[3]);
+                    v.x = *reinterpret_cast<const uint32_t*>(&p0);
+                    v.y = *reinterpret_cast<const uint32_t*>(&p1);
+                }
+                *reinterpret_cast<uint4*>(arow + ((0 ^ swz) << 4)) = v;
+#pragma unroll
+                for (int u = 1; u < 8; ++u)
+                    *reinterpret_cast<uint4*>(arow + ((u ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_full);
+            for (int l = 0; l < 4; ++l) {
+                ok = mbar_wait_or_abort(acc_full, cph, s_abort, &g_mlp_infer_wait_error, 405);
+                cph ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                if (l < 3) {
+                    // bias, ReLU, BF16 into the next layer's operand
+                    const float* bl = s_bias + l * kHid;
+#pragma unroll 1
+                    for (int j = 0; j < kHid; j += 32) {
+                        uint32_t acc[32];
+                        tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)j, acc);
+                        tmem_ld_wait();
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float x0 = fmaxf(__uint_as_float(acc[2 * e]) + bl[j + 2 * e], 0.f);
+                            const float x1 = fmaxf(__uint_as_float(acc[2 * e + 1]) + bl[j + 2 * e + 1], 0.f);
+                            const __nv_bfloat162 p = __floats2bfloat162_rn(x0, x1);
+                            pk[e] = *reinterpret_cast<const uint32_t*>(&p);
+                        }
+                        uint8_t* chunk = arow + (j / kKC) * kABytes;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int unit = ((j % kKC) >> 3) + u;
+                            *reinterpret_cast<uint4*>(chunk + ((unit ^ swz) << 4)) =
+                                make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(a_full);
+                } else {
+                    // output layer: bias, apodization scale, FP32 store
+                    const float* bl = s_bias + 3 * kHid;
+                    const float sc = (row < n && scale) ? scale[row] : 1.f;
+#pragma unroll 1
+                    for (int j = 0; j < kIO; j += 32) {
+                        uint32_t acc[32];
+                        tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)j, acc);
+                        tmem_ld_wait();
+                        if (row < n) {
+                            float4* dst = reinterpret_cast<float4*>(out + (size_t)row * ldo + j);
+#pragma unroll
+                            for (int e = 0; e < 32; e += 4)
+                                dst[e / 4] = make_float4((__uint_as_float(acc[e]) + bl[j + e]) * sc,
+                                                         (__uint_as_float(acc[e + 1]) + bl[j + e + 1]) * sc,
+                                                         (__uint_as_float(acc[e + 2]) + bl[j + e + 2]) * sc,
+                                                         (__uint_as_float(acc[e + 3]) + bl[j + e + 3]) * sc);
+                        }
+                    }
+                    tc_fence_before();
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kHid);
+    }
+}
+
+int make_map_2d_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int box_rows);
+int sm_count();
+
+int launch_mlp_infer(const double* samples, int n, const float* lo4, const float* hi4,
+                     const void* const* w16, const float* const* bias, const float* scale,
+                     float* out, int ldo, cudaStream_t st) {
+    using namespace mi;
+    CUtensorMap m[4];
+    const int rows[4] = {kHid, kHid, kHid, kIO}, cols[4] = {kIO, kHid, kHid, kHid};
+    for (int l = 0; l < 4; ++l) {
+        int rc = make_map_2d_bf16(&m[l], w16[l], rows[l], cols[l], rows[l]);
+        if (rc) return rc;
+    }
+    MlpInferArgs enc;
+    for (int k = 0; k < 4; ++k) {
+        enc.lo[k] = lo4[k];
+        enc.hi[k] = hi4[k];
+    }
+    cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    const int ntiles = (n + kM - 1) / kM;
+    const int grid = ntiles < sm_count() ? ntiles : sm_count();
+    mlp_infer_kernel<<<grid, 192, kSmem, st>>>(m[0], m[1], m[2], m[3], bias[0], bias[1], bias[2],
+                                               bias[3], samples, n, enc, scale, out, ldo);
+    return check_launch("mlp_infer_kernel");
+}
+
+}  // namespace tidas
+
+using namespace tidas;
+
+extern "C" int tidas_mlp_infer(const double* samples, int64_t n, const float* lo4, const float* hi4,
+                               const void* const* w16, const float* const* bias, const float* scale,
+                               float* out, int32_t ldo, void* stream) {
+    TIDAS_REQUIRE(samples && lo4 && hi4 && w16 && bias && out, "tidas_mlp_infer: null pointer");
+    TIDAS_REQUIRE(n >= 1 && n <= 0x7fffffff, "tidas_mlp_infer: bad n");
+    TIDAS_REQUIRE(ldo >= 64 && ldo % 4 == 0 && ((uintptr_t)out % 16) == 0,
+                  "tidas_mlp_infer: out needs ldo >= 64, ldo %% 4 == 0 and 16-byte alignment");
+    for (int l = 0; l < 4; ++l)
+        TIDAS_REQUIRE(w16[l] && bias[l] && ((uintptr_t)w16[l] % 16) == 0,
+                      "tidas_mlp_infer: layer %d weights / bias missing or misaligned", l);
+    return launch_mlp_infer(samples, (int)n, lo4, hi4, w16, bias, scale, out, ldo,
+                            (cudaStream_t)stream);
+}

@@ -420,7 +420,7 @@ int make_map_2d_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int 
     return TIDAS_OK;
 }
 
-static int sm_count() {
+int sm_count() {
     static int n = 0;
     if (!n) {
         int dev = 0;
@@ -470,6 +470,7 @@ int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int
 namespace tidas {
 int read_clear_mlp_wait_flag(int* v);
 int read_clear_das_tc_wait_flag(int* v);
+int read_clear_mlp_infer_wait_flag(int* v);
 }
 
 extern "C" int tidas_device_status(int32_t* status) {
@@ -478,13 +479,16 @@ extern "C" int tidas_device_status(int32_t* status) {
     int v = 0, zero = 0;
     TIDAS_CUDA(cudaMemcpyFromSymbol(&v, tidas::g_wait_error, sizeof(int)));
     TIDAS_CUDA(cudaMemcpyToSymbol(tidas::g_wait_error, &zero, sizeof(int)));
-    int v2 = 0, v3 = 0;
+    int v2 = 0, v3 = 0, v4 = 0;
     int rc = tidas::read_clear_mlp_wait_flag(&v2);
     if (rc) return rc;
     rc = tidas::read_clear_das_tc_wait_flag(&v3);
     if (rc) return rc;
+    rc = tidas::read_clear_mlp_infer_wait_flag(&v4);
+    if (rc) return rc;
     if (v == 0) v = v2;
     if (v == 0) v = v3;
+    if (v == 0) v = v4;
     *status = v;
     if (v != 0)
         return tidas::set_error(TIDAS_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", v);

@@ -16,6 +16,7 @@ back by that sum (tidas_apod_sum, tidas_row_scale).  Where a learned kernel's
 NRMSE against the exact kernel exceeds a threshold, the exact kernel is used
 (tidas_kernel_fallback).
 """
+import ctypes
 import math
 
 import numpy as np
@@ -190,9 +191,24 @@ class KernelMLP:
         return losses
 
     # -------------------------------------------------------------- inference
-    def infer(self, plan, samples, chunk=131072):
-        """Kernels [n, 64] (63 used) for samples [n, 4] float64 on the GPU:
-        encode, 4 BF16 GEMMs, then scale by the apodization sum."""
+    def infer(self, plan, samples, chunk=None):
+        """Kernels [n, 64] (63 used) for samples [n, 4] float64 on the GPU: one
+        fused launch (encode, four BF16 layers, scale by the apodization sum)."""
+        n = samples.shape[0]
+        out = _f32((n, OUT))
+        scale = _f32((n,))
+        capi.call("tidas_apod_sum", plan.handle, _ptr(samples), n, _ptr(scale), _stream())
+        lo = (ctypes.c_float * 4)(*BOUNDS_LO)
+        hi = (ctypes.c_float * 4)(*BOUNDS_HI)
+        w = (ctypes.c_void_p * 4)(*[_ptr(W) for W in self.W16])
+        b = (ctypes.c_void_p * 4)(*[_ptr(v) for v in self.b])
+        capi.call("tidas_mlp_infer", _ptr(samples), n, lo, hi, w, b, _ptr(scale), _ptr(out), OUT,
+                  _stream())
+        return out
+
+    def infer_layers(self, plan, samples, chunk=131072):
+        """The same kernels through the layer-by-layer GEMM (tidas_gemm_bf16):
+        the reference path of the fused kernel."""
         n = samples.shape[0]
         out = _f32((n, OUT))
         scale = _f32((n,))

@@ -79,6 +79,23 @@ def test_apod_sum_and_encode_match_oracle():
     assert not enc[:, 4:].any()
 
 
+@pytest.mark.parametrize("n", [1, 129, 70000])
+def test_fused_inference_matches_layer_path(n):
+    # tidas_mlp_infer (one launch, activations in shared memory) against the
+    # layer-by-layer GEMM path on the same BF16 weights: the same products and
+    # roundings, so agreement to FP32 accumulation-order noise; ragged last tile
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = G()
+    P = DasPlan(presets.geometry("pw128_compound"))
+    net = g.KernelMLP()
+    u = generators.uniform((n, 4), 0.0, 1.0, (64, n), np.float64)
+    lo, hi = np.array(g.BOUNDS_LO), np.array(g.BOUNDS_HI)
+    s = torch.from_numpy(lo + u * (hi - lo)).cuda()
+    fused = host(net.infer(P, s))
+    layers = host(net.infer_layers(P, s))
+    assert rel_l2(fused[:, :63], layers[:, :63]) <= 1e-5
+
+
 def _oracle_psf(xs, z, fnum, deg, taps=63):
     import oracle
     base = presets.geometry("pw128_compound")
