@@ -409,12 +409,22 @@ def bench_fista(torch, capi, generators, iters):
         x = deconv.fista(op, b, lam, 1.01 * L, iters)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        err = float(deconv.dot(x, x))  # report ||x - x_true|| / ||x_true||
+        err = float(deconv.dot(x, x))
         tmp = torch.empty_like(x)
         deconv.axpby(1.0, x, -1.0, x_true, tmp)
         rel = (float(deconv.dot(tmp, tmp)) / float(deconv.dot(x_true, x_true))) ** 0.5
+        # convergence: data residual and objective against the start x = 0
+        r = op.forward(x, None)
+        deconv.axpby(1.0, r, -1.0, b, r)
+        resid = (float(deconv.dot(r, r)) / float(deconv.dot(b, b))) ** 0.5
+        f0 = 0.5 * float(deconv.dot(b, b))
+        f = deconv.objective(op, x, b, lam)
         res[name] = {"seconds": dt, "ms_per_iter": dt / iters * 1e3, "L": L, "lambda": lam,
-                     "rel_err_vs_truth": rel, "x_norm2": err}
+                     "data_residual": resid, "objective_ratio": f / f0,
+                     "rel_err_vs_truth": rel, "x_norm2": err,
+                     "note": "the band-limited PSF makes the sparse map unrecoverable in "
+                             "200 iterations (rel_err_vs_truth near 1 for any operator); "
+                             "data_residual and objective_ratio show the solve"}
     res["speedup_tidas_gemm_resid_vs_exact"] = res["exact"]["seconds"] / res["tidas_gemm_resid"]["seconds"]
     return res
 
