@@ -62,6 +62,8 @@ def lib():
             "orc_das_adjoint": (None, [_G, _D, _D]),
             "orc_tidas_conv": (None, [ctypes.c_int] * 4 + [_D, _D, _D]),
             "orc_tidas_conv_adjoint": (None, [ctypes.c_int] * 4 + [_D, _D, _D]),
+            "orc_tidas_conv2d": (None, [ctypes.c_int] * 6 + [_D, _D, _D]),
+            "orc_tidas_conv2d_adjoint": (None, [ctypes.c_int] * 6 + [_D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -231,6 +233,27 @@ class Oracle:
             out.append(vals)
         return np.array(out)
 
+    def psf_patches(self, kz, taps, rows=None, ic=None):
+        """2D band kernels: for every row j, the exact image of a unit scatterer
+        on pixel (ic, j) (Eq. (2.1) then Eq. (2.2)) over output rows
+        j + u - kz//2 (u = 0..kz-1, also outside the grid) and columns
+        ic + t - taps//2 (zero outside the grid): kernels[j][u][t]."""
+        ic = self.center_column() if ic is None else ic
+        rows = range(self.nz) if rows is None else rows
+        cz, half = kz // 2, taps // 2
+        cols = np.arange(ic - half, ic - half + taps)
+        ok = (cols >= 0) & (cols < self.nx)
+        out = []
+        for j in rows:
+            rf = self.synthesize([[self.pix_x(ic), self.pix_z(j)]], [[1.0, 0.0]])
+            # a grid of kz rows x taps columns centred on the scatterer
+            patch = dict(self.p, nz=kz, z0=self.p["z0"] + (j - cz) * self.p["dz"],
+                         nx=taps, x0=self.p["x0"] + (ic - half) * self.p["dx"])
+            img = Oracle(patch).das(rf)
+            img[:, ~ok] = 0.0
+            out.append(img)
+        return np.array(out)
+
     def fit_kernels(self, taps, ref_stride=1, rows=None):
         """Per-row kernels.  ref_stride == 1: the PSF row itself.  ref_stride > 1:
         rows share the PSF of a reference row s (the middle row of each block of
@@ -293,6 +316,32 @@ def tidas_conv_adjoint(kernels, y, center=None):
         return np.stack([tidas_conv_adjoint(kernels, x, center) for x in y])
     r = np.empty_like(y)
     lib().orc_tidas_conv_adjoint(nz, y.shape[1], taps, center, _dp(kernels), _dp(y), _dp(r))
+    return r
+
+
+def tidas_conv2d(kernels, r):
+    """2D band form of Eq. (2.13): every pixel of r adds its row's
+    single-scatterer image kernels[j] (kz rows x taps columns, centred)."""
+    kernels = _f64(kernels)
+    r = _f64(r)
+    nz, kz, taps = kernels.shape
+    if r.ndim == 3:
+        return np.stack([tidas_conv2d(kernels, x) for x in r])
+    y = np.empty_like(r)
+    lib().orc_tidas_conv2d(nz, r.shape[1], kz, taps, kz // 2, taps // 2, _dp(kernels), _dp(r),
+                           _dp(y))
+    return y
+
+
+def tidas_conv2d_adjoint(kernels, y):
+    kernels = _f64(kernels)
+    y = _f64(y)
+    nz, kz, taps = kernels.shape
+    if y.ndim == 3:
+        return np.stack([tidas_conv2d_adjoint(kernels, x) for x in y])
+    r = np.empty_like(y)
+    lib().orc_tidas_conv2d_adjoint(nz, y.shape[1], kz, taps, kz // 2, taps // 2, _dp(kernels),
+                                   _dp(y), _dp(r))
     return r
 
 

@@ -325,3 +325,48 @@ void orc_tidas_conv_adjoint(int nz, int nx, int taps, int center, const double* 
             r[(size_t)iz * nx + j] = acc;
         }
 }
+
+/* 2D band kernels (the PSF's axial extent kept): kernels[j][u][t] is the image
+ * of a unit scatterer on row j at output row j + u - cz, column offset
+ * t - cx from the scatterer.  Superposing the images of all pixels of r:
+ *   y[i][x] = sum_{u, t} kernels[j][u][t] * r[j][x - t + cx],  j = i - u + cz,
+ * rows j outside [0, nz) and columns outside [0, nx) contributing nothing.
+ * kz = 1, cz = 0 is the row-wise convolution orc_tidas_conv. */
+void orc_tidas_conv2d(int nz, int nx, int kz, int taps, int cz, int cx, const double* kernels,
+                      const double* r, double* y) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < nz; ++i)
+        for (int x = 0; x < nx; ++x) {
+            double acc = 0.0;
+            for (int u = 0; u < kz; ++u) {
+                int j = i - u + cz;
+                if (j < 0 || j >= nz) continue;
+                for (int t = 0; t < taps; ++t) {
+                    int xs = x - t + cx;
+                    if (xs < 0 || xs >= nx) continue;
+                    acc += kernels[((size_t)j * kz + u) * taps + t] * r[(size_t)j * nx + xs];
+                }
+            }
+            y[(size_t)i * nx + x] = acc;
+        }
+}
+/* Transpose of orc_tidas_conv2d:
+ *   r[j][xs] = sum_{u, t} kernels[j][u][t] * y[j + u - cz][xs + t - cx]. */
+void orc_tidas_conv2d_adjoint(int nz, int nx, int kz, int taps, int cz, int cx,
+                              const double* kernels, const double* y, double* r) {
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < nz; ++j)
+        for (int xs = 0; xs < nx; ++xs) {
+            double acc = 0.0;
+            for (int u = 0; u < kz; ++u) {
+                int i = j + u - cz;
+                if (i < 0 || i >= nz) continue;
+                for (int t = 0; t < taps; ++t) {
+                    int x = xs + t - cx;
+                    if (x < 0 || x >= nx) continue;
+                    acc += kernels[((size_t)j * kz + u) * taps + t] * y[(size_t)i * nx + x];
+                }
+            }
+            r[(size_t)j * nx + xs] = acc;
+        }
+}

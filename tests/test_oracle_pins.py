@@ -363,6 +363,78 @@ def test_tidas_kernel_reproduces_exact_psf_row():
         assert np.all(y[:sl.start] == 0) and np.all(y[sl.stop:] == 0)
 
 
+# ---------------------------------------------- 2D band kernels (axial x lateral)
+def test_tidas_conv2d_kz1_is_the_rowwise_convolution():
+    import oracle
+    rng = np.random.default_rng(7)
+    h = rng.standard_normal((6, 1, 9))
+    r = rng.standard_normal((2, 6, 30))
+    np.testing.assert_allclose(oracle.tidas_conv2d(h, r), oracle.tidas_conv(h[:, 0], r),
+                               rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("kz,taps", [(5, 7), (4, 3), (16, 31)])
+def test_tidas_conv2d_matches_scattered_convolutions(kz, taps):
+    # scatter form, written independently of the oracle's gather loop: every
+    # input row j, convolved laterally with slice u of its own kernel, lands on
+    # output row j + u - kz//2
+    import oracle
+    rng = np.random.default_rng(8)
+    nz, nx = 11, 37
+    h = rng.standard_normal((nz, kz, taps))
+    r = rng.standard_normal((nz, nx))
+    want = np.zeros((nz, nx))
+    cz, cx = kz // 2, taps // 2
+    for j in range(nz):
+        for u in range(kz):
+            i = j + u - cz
+            if 0 <= i < nz:
+                want[i] += np.convolve(r[j], h[j, u])[cx:cx + nx]
+    np.testing.assert_allclose(oracle.tidas_conv2d(h, r), want, rtol=1e-12, atol=1e-12)
+    # a unit reflector reproduces its row's kernel, centred on it
+    e = np.zeros((nz, nx))
+    e[5, 18] = 1.0
+    y = oracle.tidas_conv2d(h, e)
+    for u in range(kz):
+        i = 5 + u - cz
+        if 0 <= i < nz:
+            np.testing.assert_array_equal(y[i, 18 - cx:18 - cx + taps], h[5, u])
+    # adjoint identity
+    v = rng.standard_normal((nz, nx))
+    lhs = np.vdot(oracle.tidas_conv2d(h, r), v)
+    rhs = np.vdot(r, oracle.tidas_conv2d_adjoint(h, v))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_psf_patch_reproduces_exact_image():
+    # the 2D kernel of row j convolved with the fitting scatterer returns the
+    # exact DAS image of that scatterer over the whole patch; its centre row
+    # is the 1D kernel of the same row
+    import oracle
+    g = presets.geometry("pw64_single")
+    o = O(g)
+    kz, taps = 9, 31
+    rows = [40, 150]
+    pat = o.psf_patches(kz, taps, rows=rows)
+    psf = o.psf_rows(taps, rows=rows)
+    ic = o.center_column()
+    for n, j in enumerate(rows):
+        rf = o.synthesize([[o.pix_x(ic), o.pix_z(j)]], [[1.0, 0.0]])
+        img = o.das(rf)
+        k = np.zeros((o.nz, kz, taps))
+        k[j] = pat[n]
+        r = np.zeros((o.nz, o.nx))
+        r[j, ic] = 1.0
+        y = oracle.tidas_conv2d(k, r)
+        rs = slice(j - kz // 2, j - kz // 2 + kz)
+        cs = slice(ic - taps // 2, ic - taps // 2 + taps)
+        # the patch grid rounds its own pixel coordinates (x0 + (i + 1/2) dx with
+        # a shifted x0), so delays differ in the last bits: ~1e-12 of the peak
+        peak = np.abs(img).max()
+        np.testing.assert_allclose(y[rs, cs], img[rs, cs], rtol=0, atol=1e-10 * peak)
+        np.testing.assert_allclose(pat[n][kz // 2], psf[n], rtol=1e-13, atol=1e-13)
+
+
 def test_fwhm_of_gaussian():
     import oracle
     x = np.arange(-50, 51, dtype=np.float64)
