@@ -30,6 +30,7 @@ GEOM = "pw128_compound"
 BATCH = 64
 TIDAS_FRAMES = 256
 TAPS = 63
+KZ = 16  # rows of the 2D band kernels
 
 
 def parse():
@@ -374,6 +375,69 @@ def bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak, bf
     ops.tidas_forward(kern, refl[:1].contiguous(), variant=capi.VARIANT_DIRECT, out=out[:1])
     d = das_img[0].double()
     res["nrmse_vs_exact_das"] = float((out[0].double() - d).norm() / d.norm())
+    res["band_2d"] = bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, d, args, stream,
+                                   bf16_peak)
+    return res
+
+
+def _band_rows_oracle(kern, x, rows):
+    """FP64 oracle of output rows `rows` of the 2D band forward map, each from
+    the slab of input rows its band reaches."""
+    import oracle
+    nz, kz, _ = kern.shape
+    cz = kz // 2
+    out = []
+    for i in rows:
+        lo, hi = max(0, i - (kz - 1) + cz), min(nz - 1, i + cz)
+        out.append(oracle.tidas_conv2d(kern[lo:hi + 1], x[:, lo:hi + 1])[:, i - lo])
+    return np.stack(out, axis=1)
+
+
+def bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, das0, args, stream, bf16_peak):
+    """2D band kernels (KZ x TAPS per depth row) on the same 256-frame batch:
+    kernel fit, direct FP32 and tcgen05 Toeplitz GEMM forward maps, accuracy
+    against the oracle and against the exact DAS image."""
+    nf, nz, nx = refl.shape
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    k2 = P32.fit_kernels_2d(KZ, TAPS)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    res = {"kz": KZ, "taps": TAPS, "fit_ms": t0.elapsed_time(t1)}
+    cz = KZ // 2
+    # valid band slices summed over the output rows (rows near the edges have fewer)
+    nu = sum(min(KZ - 1, z + cz) - max(0, z + cz - (nz - 1)) + 1 for z in range(nz))
+    useful = 2.0 * nf * nu * nx * TAPS
+    # MMA work as issued: per (output row, 128 frames, 2 column tiles, slice)
+    # every tile takes 3 chunks of 64 input columns
+    ntiles = -(-nx // 128)
+    mma = 2.0 * 128 * 128 * 192 * ntiles * (-(-nf // 128)) * nu
+    kh = k2.cpu().numpy()
+    for variant, x, name in ((capi.VARIANT_DIRECT, refl, "direct_f32"),
+                             (capi.VARIANT_GEMM_BF16, refl_bf, "gemm_bf16")):
+        fn = lambda: ops.tidas_forward_2d(k2, x, variant=variant, out=out)  # noqa: E731
+        try:
+            fn()
+        except capi.TidasError as e:
+            res[name] = {"unavailable": str(e)}
+            continue
+        m = time_steps(torch, fn, max(3, args.steps), 2, stream)
+        r = {"ms": m, "mpix_s": nf * nz * nx / (m * 1e-3) / 1e6,
+             "useful_tflops": useful / (m * 1e-3) / 1e12}
+        if variant == capi.VARIANT_GEMM_BF16:
+            a = mma / (m * 1e-3) / 1e12
+            r["tensor"] = {"mma_tflops": a, "peak_tflops": bf16_peak, "frac": a / bf16_peak,
+                           "mma_flops_per_launch": mma}
+        rows = [0, 333, nz - 1]
+        frames = np.array([0, nf - 1])
+        xin = x[frames].double().cpu().numpy()
+        ref = _band_rows_oracle(kh, xin, rows)
+        got = out[frames][:, rows].double().cpu().numpy()
+        r["nrmse_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        res[name] = r
+    ops.tidas_forward_2d(k2, refl[:1].contiguous(), variant=capi.VARIANT_DIRECT, out=out[:1])
+    res["nrmse_vs_exact_das"] = float((out[0].double() - das0).norm() / das0.norm())
     return res
 
 

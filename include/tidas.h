@@ -182,6 +182,31 @@ int tidas_forward(const float* kernels, int32_t taps, int32_t nz, int32_t nx, co
 int tidas_adjoint(const float* kernels, int32_t taps, int32_t nz, int32_t nx, const void* img,
                   float* refl, int32_t n_frames, int32_t variant, void* stream);
 
+/* 2D band kernels (axial x lateral):
+ * keep the PSF's axial extent that the row-wise kernels drop.  kernels
+ * [nz][kz][taps] float32; slice u of row j is the image of a unit scatterer on
+ * pixel (nx/2, j) at output row j + u - kz/2 and columns nx/2 + t - taps/2
+ * (Sections 2.2-2.3, Eq. (2.6)-(2.7), with the axial dimension kept).
+ * tidas_fit_kernels_2d computes them with the plan's exact DAS (FP64 delays;
+ * columns outside the grid are zero, rows outside it are evaluated).
+ * 1 <= kz <= 64, 1 <= taps <= 255. */
+int tidas_fit_kernels_2d(das_plan plan, int32_t kz, int32_t taps, float* kernels, void* stream);
+
+/* Eq. (2.13) with the 2D band kernels, every pixel of r adding its row's
+ * single-scatterer image:
+ *   img[f][i][x] = sum_{u, t} kernels[j][u][t] refl[f][j][x - t + taps/2],
+ *                  j = i - u + kz/2 (rows and columns outside the grid skipped);
+ * tidas_adjoint_2d is the transpose.  variant: TIDAS_VARIANT_DIRECT (FP32
+ * CUDA cores, refl float32) or TIDAS_VARIANT_GEMM_BF16 (tcgen05 Toeplitz
+ * GEMMs over the kz input rows; refl BF16, taps <= 63, nx % 8 == 0, 16-byte
+ * aligned arrays).  nx <= 2048. */
+int tidas_forward_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz, int32_t nx,
+                     const void* refl, float* img, int32_t n_frames, int32_t variant,
+                     void* stream);
+int tidas_adjoint_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz, int32_t nx,
+                     const void* img, float* refl, int32_t n_frames, int32_t variant,
+                     void* stream);
+
 /* ------------------------------------------------------------------------
  * Deconvolution on the convolutional model (the use the paper names for it in
  * its abstract, introduction and conclusion): min_x 1/2 ||H x - b||^2 +

@@ -68,6 +68,9 @@ _SIG = {
     "tidas_mse": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
     "tidas_encode": [_P, _I, _P, _P, _P, _P],
     "tidas_mlp_infer": [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _I, _P],
+    "tidas_fit_kernels_2d": [_P, _I, _I, _P, _P],
+    "tidas_forward_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P],
+    "tidas_adjoint_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_forward_varying": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
     "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
     "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],
@@ -153,6 +156,20 @@ def tidas_forward(kernels, taps, nz, nx, refl, img, n_frames, variant, stream=0)
 
 def tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream=0):
     return _check(load().tidas_adjoint(kernels, taps, nz, nx, img, refl, n_frames, variant, stream))
+
+
+def tidas_fit_kernels_2d(plan, kz, taps, kernels, stream=0):
+    return _check(load().tidas_fit_kernels_2d(plan, kz, taps, kernels, stream))
+
+
+def tidas_forward_2d(kernels, kz, taps, nz, nx, refl, img, n_frames, variant, stream=0):
+    return _check(load().tidas_forward_2d(kernels, kz, taps, nz, nx, refl, img, n_frames, variant,
+                                          stream))
+
+
+def tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant, stream=0):
+    return _check(load().tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant,
+                                          stream))
 
 
 def tidas_dot(a, b, n, out, stream=0):

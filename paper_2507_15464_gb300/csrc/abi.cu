@@ -6,6 +6,11 @@ int launch_tidas_direct(const float* kern, int taps, int center, bool adjoint, i
                         const float* in, float* out, int nf, cudaStream_t st);
 int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int nz, int nx,
                       const void* in, float* out, int nf, bool resid, cudaStream_t st);
+int launch_tidas_direct2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
+                          const float* in, float* out, int nf, cudaStream_t st);
+int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
+                        const void* in, float* out, int nf, cudaStream_t st);
+int launch_fit_kernels_2d(const Plan& P, int kz, int taps, float* kernels, cudaStream_t st);
 }  // namespace tidas
 
 using namespace tidas;
@@ -115,4 +120,50 @@ extern "C" int tidas_adjoint(const float* kernels, int32_t taps, int32_t nz, int
                              void* stream) {
     return tidas_common("tidas_adjoint", kernels, taps, nz, nx, img, refl, n_frames, variant, true,
                         stream);
+}
+
+// ------------------------------------------------ 2D band kernels
+extern "C" int tidas_fit_kernels_2d(das_plan plan, int32_t kz, int32_t taps, float* kernels,
+                                    void* stream) {
+    PLAN_OR_FAIL(plan);
+    TIDAS_REQUIRE(kernels, "tidas_fit_kernels_2d: null kernels");
+    TIDAS_REQUIRE(taps >= 1 && taps <= 255 && kz >= 1 && kz <= 64,
+                  "tidas_fit_kernels_2d: need 1 <= taps <= 255 and 1 <= kz <= 64");
+    return launch_fit_kernels_2d(P, kz, taps, kernels, S_(stream));
+}
+
+static int tidas2d_common(const char* who, const float* kernels, int32_t kz, int32_t taps,
+                          int32_t nz, int32_t nx, const void* in, float* out, int32_t n_frames,
+                          int32_t variant, bool adjoint, void* stream) {
+    TIDAS_REQUIRE(kernels && in && out, "%s: null pointer", who);
+    TIDAS_REQUIRE(taps >= 1 && taps <= 255 && kz >= 1 && kz <= 64, "%s: bad kernel shape", who);
+    TIDAS_REQUIRE(nz >= 1 && nz <= 65535 && nx >= 1 && nx <= 2048, "%s: bad grid", who);
+    TIDAS_REQUIRE(n_frames >= 1 && n_frames <= 65535, "%s: bad frame count", who);
+    if (variant == TIDAS_VARIANT_DIRECT)
+        return launch_tidas_direct2d(kernels, kz, taps, adjoint, nz, nx, (const float*)in, out,
+                                     n_frames, S_(stream));
+    if (variant == TIDAS_VARIANT_GEMM_BF16) {
+        TIDAS_REQUIRE(taps <= 63, "%s: the GEMM variant needs taps <= 63", who);
+        TIDAS_REQUIRE(nx % 8 == 0, "%s: the GEMM variant needs nx %% 8 == 0", who);
+        TIDAS_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0,
+                      "%s: the GEMM variant needs 16-byte aligned arrays", who);
+        return launch_tidas_gemm2d(kernels, kz, taps, adjoint, nz, nx, in, out, n_frames,
+                                   S_(stream));
+    }
+    return set_error(TIDAS_ERR_ARG, "%s: variant %d is not available for 2D kernels", who,
+                     variant);
+}
+
+extern "C" int tidas_forward_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz,
+                                int32_t nx, const void* refl, float* img, int32_t n_frames,
+                                int32_t variant, void* stream) {
+    return tidas2d_common("tidas_forward_2d", kernels, kz, taps, nz, nx, refl, img, n_frames,
+                          variant, false, stream);
+}
+
+extern "C" int tidas_adjoint_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz,
+                                int32_t nx, const void* img, float* refl, int32_t n_frames,
+                                int32_t variant, void* stream) {
+    return tidas2d_common("tidas_adjoint_2d", kernels, kz, taps, nz, nx, img, refl, n_frames,
+                          variant, true, stream);
 }

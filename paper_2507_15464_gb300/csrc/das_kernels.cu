@@ -473,6 +473,7 @@ int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int n
 // p(m - u_scat) at the interpolation taps m around u_pix.  Delays in FP64.
 struct FitArgs {
     int n_elem, n_angles, nx, nz, taps, ic, interp, n_samples;
+    int kz;  // output rows per kernel: rows iz + u - kz/2, u = 0..kz-1 (1: the row itself)
     double pitch, c, fs, t0, x0, dx, z0, dz, fnum;
     double thalf, beta, wcar;  // samples
 };
@@ -495,11 +496,13 @@ __device__ __forceinline__ double pulse_fp(const FitArgs& A, double t) {
 __global__ void fit_psf_kernel(FitArgs A, const double* __restrict__ sncs, float* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
+    const int u = blockIdx.z;  // output row iz + u - kz/2 (also outside the grid)
     if (t >= A.taps) return;
     const int ix = A.ic + t - A.taps / 2;
     float result = 0.f;
-    if (ix >= 0 && ix < A.nx) {
-        const double z = A.z0 + ((double)iz + 0.5) * A.dz;
+    const double zsc = A.z0 + ((double)iz + 0.5) * A.dz;                  // scatterer
+    const double z = A.z0 + ((double)(iz + u - A.kz / 2) + 0.5) * A.dz;   // pixel
+    if (ix >= 0 && ix < A.nx && z > 0.0) {
         const double xs = A.x0 + ((double)A.ic + 0.5) * A.dx;  // scatterer
         const double xp = A.x0 + ((double)ix + 0.5) * A.dx;    // pixel
         double acc = 0.0;
@@ -515,7 +518,7 @@ __global__ void fit_psf_kernel(FitArgs A, const double* __restrict__ sncs, float
                     w = cw * cw;
                 }
                 const double up = delay_fp64(A, sn, cs, n, xp, z);
-                const double us = delay_fp64(A, sn, cs, n, xs, z);
+                const double us = delay_fp64(A, sn, cs, n, xs, zsc);
                 const double fl = floor(up);
                 const double phi = up - fl;
                 const int i = (int)fl;
@@ -539,7 +542,7 @@ __global__ void fit_psf_kernel(FitArgs A, const double* __restrict__ sncs, float
         }
         result = (float)acc;
     }
-    out[(size_t)iz * A.taps + t] = result;
+    out[((size_t)iz * A.kz + u) * A.taps + t] = result;
 }
 
 // Rows other than the reference rows become theta * (reference PSF), with
@@ -582,9 +585,9 @@ __global__ void fill_ones_kernel(float* p, int n) {
     if (i < n) p[i] = 1.f;
 }
 
-int launch_fit_kernels(const Plan& P, int taps, int ref_stride, float* kernels, float* theta,
-                       cudaStream_t st) {
+static FitArgs fit_args(const Plan& P, int taps, int kz) {
     FitArgs A;
+    A.kz = kz;
     A.n_elem = P.p.n_elem;
     A.n_angles = P.p.n_angles;
     A.nx = P.p.nx;
@@ -605,7 +608,13 @@ int launch_fit_kernels(const Plan& P, int taps, int ref_stride, float* kernels, 
     A.thalf = P.thalf_samples;
     A.beta = P.beta_samples;
     A.wcar = P.wcar;
-    dim3 grid((taps + 63) / 64, P.p.nz);
+    return A;
+}
+
+int launch_fit_kernels(const Plan& P, int taps, int ref_stride, float* kernels, float* theta,
+                       cudaStream_t st) {
+    const FitArgs A = fit_args(P, taps, 1);
+    dim3 grid((taps + 63) / 64, P.p.nz, 1);
     fit_psf_kernel<<<grid, 64, 0, st>>>(A, P.d_sncs, kernels);
     int rc = check_launch("fit_psf_kernel");
     if (rc) return rc;
@@ -617,6 +626,15 @@ int launch_fit_kernels(const Plan& P, int taps, int ref_stride, float* kernels, 
         rc = check_launch("fill_ones_kernel");
     }
     return rc;
+}
+
+// 2D band kernels [nz][kz][taps]: the single-scatterer image of every row over
+// kz output rows centred on it.
+int launch_fit_kernels_2d(const Plan& P, int kz, int taps, float* kernels, cudaStream_t st) {
+    const FitArgs A = fit_args(P, taps, kz);
+    dim3 grid((taps + 63) / 64, P.p.nz, kz);
+    fit_psf_kernel<<<grid, 64, 0, st>>>(A, P.d_sncs, kernels);
+    return check_launch("fit_psf_kernel");
 }
 
 }  // namespace tidas

@@ -180,4 +180,157 @@ int launch_tidas_direct(const float* kern, int taps, int center, bool adjoint, i
     return check_launch("tidas_direct_kernel");
 }
 
+// 2D band kernels (the PSF's axial extent): kernels [nz][kz][taps], slice u of
+// row j = the image of a unit scatterer on row j at output row j + u - kz/2.
+//   forward:  y[i][x]  = sum_u sum_t h[j][u][t] r[j][x - t + c],  j = i - u + kz/2
+//   adjoint:  r[j][x'] = sum_u sum_t h[j][u][t] y[i][x' + t - c], i = j + u - kz/2
+// Same block structure as the row-wise kernel, with a staging sequence over
+// (frame group, u): every step stages the input lines of row i - u + kz/2
+// (forward) or i + u - kz/2 (adjoint) and the kernel slice it needs, and the
+// output registers accumulate over the valid u of a group before the store.
+// A group holds nfg <= kFB frames, so that nfg * (nx / kV) outputs fit one
+// per thread.
+template <int WC>
+__global__ void __launch_bounds__(kThreads, 4) tidas_direct2d_kernel(
+    const float* __restrict__ kern, int kz, int taps, int off, bool adjoint, int nz, int nx,
+    const float* __restrict__ in, float* __restrict__ out, int nf, int nfg, int groups_per_block) {
+    extern __shared__ float sm[];
+    const int tpad = (taps + kV - 1) / kV * kV;
+    const int len = nx + tpad + 2 * kV;
+    const int W = WC > 0 ? WC : ((len + kV - 1) / kV) | 1;
+    const int step_len = tpad + nfg * kV * W;    // kernel slice + nfg lines
+    float* bufs = sm;                             // [2][step_len]
+    const int io = blockIdx.x;                    // output row
+    const int cz = kz / 2;
+    const int ngroups = (nf + nfg - 1) / nfg;
+    const int g0 = blockIdx.y * groups_per_block;
+    const int g1 = min(ngroups, g0 + groups_per_block);
+    // valid u: input rows inside [0, nz)
+    const int u_lo = adjoint ? max(0, cz - io) : max(0, io + cz - (nz - 1));
+    const int u_hi = adjoint ? min(kz - 1, nz - 1 - io + cz) : min(kz - 1, io + cz);
+    const int nu = u_hi >= u_lo ? u_hi - u_lo + 1 : 0;
+    const int nsteps = (g1 - g0) * (nu > 0 ? nu : 1);
+
+    // step k: group g0 + k / nu, slice u_lo + k % nu
+    auto stage = [&](int k, int b) {
+        float* hr = bufs + b * step_len;
+        float* lines = hr + tpad;
+        const int g = g0 + k / max(nu, 1), u = u_lo + k % max(nu, 1);
+        const int irow = adjoint ? io + u - cz : io - u + cz;   // input row
+        const int krow = adjoint ? io : irow;                   // kernel row
+        const float* ks = kern + ((size_t)krow * kz + u) * taps;
+        for (int s = threadIdx.x; s < tpad; s += blockDim.x) {
+            float v = 0.f;
+            if (nu > 0 && s < taps) v = __ldg(ks + (adjoint ? s : taps - 1 - s));
+            hr[s] = v;
+        }
+        for (int fb = 0; fb < nfg; ++fb) {
+            const int f = g * nfg + fb;
+            const float* src = in + ((size_t)min(f, nf - 1) * nz + (nu > 0 ? irow : 0)) * nx;
+            float* ln = lines + fb * kV * W;
+            const bool live = nu > 0 && f < nf;
+            for (int j = threadIdx.x; j < kV * W; j += blockDim.x) {
+                const int x = j - off;
+                const bool inside = live && x >= 0 && x < nx;
+                cp_async4(ln + (j % kV) * W + j / kV, src + (inside ? x : 0), inside ? 4 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+
+    const int chunks = (nx + kV - 1) / kV;
+    const bool vec = (nx % 4) == 0;
+    // one output item per thread and group: nfg frames x chunks of kV columns
+    const int item = threadIdx.x;
+    const int fb = item / chunks, c = item % chunks;
+    float y[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) y[v] = 0.f;
+    if (nsteps > 0) stage(0, 0);
+    for (int k = 0; k < nsteps; ++k) {
+        const int b = k & 1;
+        if (k + 1 < nsteps) {
+            stage(k + 1, b ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int g = g0 + k / max(nu, 1);
+        const int nfb = min(nfg, nf - g * nfg);
+        const float* hr = bufs + b * step_len;
+        if (item < nfb * chunks && nu > 0) {
+            const float* ln = hr + tpad + fb * kV * W + c;
+            for (int s = 0; s < tpad; s += kV) {
+                const int sb = s / kV;
+                float a[2 * kV], h[kV];
+#pragma unroll
+                for (int q = 0; q < 2 * kV; ++q) a[q] = ln[(q % kV) * W + sb + q / kV];
+#pragma unroll
+                for (int q = 0; q < kV; q += 4) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(hr + s + q);
+                    h[q] = t4.x;
+                    h[q + 1] = t4.y;
+                    h[q + 2] = t4.z;
+                    h[q + 3] = t4.w;
+                }
+#pragma unroll
+                for (int q = 0; q < kV; ++q)
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) y[v] = fmaf(h[q], a[v + q], y[v]);
+            }
+        }
+        if (nu == 0 || k % nu == nu - 1) {  // the group's last slice: store, restart
+            if (item < nfb * chunks) {
+                const int x0 = c * kV;
+                float* dst = out + ((size_t)(g * nfg + fb) * nz + io) * nx + x0;
+                if (vec && x0 + kV <= nx) {
+#pragma unroll
+                    for (int v = 0; v < kV; v += 4)
+                        *reinterpret_cast<float4*>(dst + v) =
+                            make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kV; ++v)
+                        if (x0 + v < nx) dst[v] = y[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < kV; ++v) y[v] = 0.f;
+        }
+        __syncthreads();  // buffer b is refilled two steps later
+    }
+}
+
+int launch_tidas_direct2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
+                          const float* in, float* out, int nf, cudaStream_t st) {
+    const int tpad = (taps + kV - 1) / kV * kV;
+    const int len = nx + tpad + 2 * kV;
+    const int W = ((len + kV - 1) / kV) | 1;
+    const int chunks = (nx + kV - 1) / kV;
+    if (chunks > kThreads)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "tidas 2D direct: rows up to %d columns",
+                         kThreads * kV);
+    const int nfg = min(kFB, kThreads / chunks);
+    constexpr int kWC = 65;
+    const bool fixed = W <= kWC;
+    const size_t smem = (size_t)2 * (tpad + nfg * kV * (fixed ? kWC : W)) * sizeof(float);
+    if (smem > 220 * 1024) return set_error(TIDAS_ERR_UNSUPPORTED, "tidas 2D direct: row too long");
+    if (nx % 4 == 0 && ((uintptr_t)out % 16) != 0)
+        return set_error(TIDAS_ERR_ARG, "tidas 2D direct: output must be 16-byte aligned");
+    auto kernel = fixed ? tidas_direct2d_kernel<kWC> : tidas_direct2d_kernel<0>;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // forward: taps reversed, off = taps-1-c; adjoint: taps as stored, off = c
+    const int center = taps / 2;
+    const int off = adjoint ? center : taps - 1 - center;
+    const int ngroups = (nf + nfg - 1) / nfg;
+    int runs = 1;
+    while (runs < ngroups && (long long)nz * runs < 4LL * 152 * 4) runs *= 2;
+    const int per = (ngroups + runs - 1) / runs;
+    dim3 grid(nz, (ngroups + per - 1) / per);
+    kernel<<<grid, kThreads, smem, st>>>(kern, kz, taps, off, adjoint, nz, nx, in, out, nf, nfg,
+                                         per);
+    return check_launch("tidas_direct2d_kernel");
+}
+
 }  // namespace tidas

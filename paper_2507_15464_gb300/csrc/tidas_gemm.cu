@@ -270,19 +270,18 @@ __global__ void __launch_bounds__(gemm::Cfg<RESID>::kThreads, 1)
         // --------------------------------------- Toeplitz operand builders
         const int bt = threadIdx.x - 6 * 32;  // 0..63
         int prev_z = -1, nrow = -1;
-        for (int it = it_begin; it < it_end && !*s_abort; ++it) {
+        for (int it = it_begin; it < it_end; ++it) {
             const Item I = decode(it, nh, nm, ntiles);
             if (I.z == prev_z) continue;
             prev_z = I.z;
             ++nrow;
             const int b = nrow % C::kBBufs;
-            if (!mbar_wait(&b_empty[b], ((nrow / C::kBBufs) & 1) ^ 1, &g_wait_error, kWaitB)) {
-                *s_abort = 1;
-                break;
-            }
+            const bool ok = mbar_wait_or_abort(&b_empty[b], ((nrow / C::kBBufs) & 1) ^ 1, s_abort,
+                                               &g_wait_error, kWaitB);
             float* tp = s_taps + b * 64;
-            if (bt < 64) tp[bt] = bt < taps ? __ldg(kern + (size_t)I.z * taps + bt) : 0.f;
-            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (ok && bt < 64) tp[bt] = bt < taps ? __ldg(kern + (size_t)I.z * taps + bt) : 0.f;
+            // the taps are in; leave together if any builder or role gave up
+            if (named_bar_or<1>(64, !ok || *s_abort)) break;
             uint8_t* dst = sB + (size_t)b * C::kBParts * 3 * kBTileBytes;
             for (int idx = bt; idx < 3 * kN * kKC / 2; idx += 64) {
                 // two consecutive k per thread
@@ -463,6 +462,293 @@ int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int
             map_in, map_out, nullptr, kern, taps, center, adjoint ? 1 : 0, nz, nx, nf);
     }
     return check_launch("tidas_gemm_kernel");
+}
+
+// ------------------------------------------------- 2D band kernels (tcgen05)
+// Y_z = sum_u R_{j(u)} T_{j(u), u}: the row-wise Toeplitz GEMM summed over the
+// kz input rows j = z - u + kz/2 (adjoint: j = z + u - kz/2, kernel row z)
+// into the same accumulators.  A step = (item, u): the producer streams the
+// item's input chunks of row j, six builder warps write that step's three
+// Toeplitz tiles (double buffered), the MMA warp issues the item's MMAs.
+namespace gemm2 {
+constexpr int kStages = 4;
+constexpr int kBBufs = 2;
+constexpr int kBuilders = 6;  // warps 6 .. 11
+constexpr int kThreads = 32 * (6 + kBuilders);
+constexpr size_t kOffA = 0;
+constexpr size_t kOffB = kOffA + (size_t)kStages * gemm::kChunkBytes;
+constexpr size_t kOffO = kOffB + (size_t)kBBufs * 3 * gemm::kBTileBytes;
+constexpr size_t kOffBar = kOffO + (size_t)4 * 2 * gemm::kOutTileBytes;
+constexpr size_t kSmem = 1024 + kOffBar + 1024;
+}  // namespace gemm2
+
+__device__ __forceinline__ void u_range2d(int z, int kz, int nz, bool adjoint, int& lo, int& hi) {
+    const int cz = kz / 2;
+    if (adjoint) {
+        lo = max(0, cz - z);
+        hi = min(kz - 1, nz - 1 - z + cz);
+    } else {
+        lo = max(0, z + cz - (nz - 1));
+        hi = min(kz - 1, z + cz);
+    }
+}
+
+__global__ void __launch_bounds__(gemm2::kThreads, 1)
+    tidas_gemm2d_kernel(const __grid_constant__ CUtensorMap tmap_in,
+                        const __grid_constant__ CUtensorMap tmap_out, const float* __restrict__ kern,
+                        int kz, int taps, int adjoint, int nz, int nx, int nf) {
+    using namespace gemm;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base + gemm2::kOffA;  // [stage] BF16 input chunks
+    uint8_t* sB = base + gemm2::kOffB;  // [buf][3] Toeplitz tiles
+    uint8_t* sO = base + gemm2::kOffO;  // [epilogue warp][2] output staging tiles
+    uint64_t* full = (uint64_t*)(base + gemm2::kOffBar);
+    uint64_t* empty = full + gemm2::kStages;
+    uint64_t* b_full = empty + gemm2::kStages;
+    uint64_t* b_empty = b_full + 2;
+    uint64_t* acc_full = b_empty + 2;
+    uint64_t* acc_empty = acc_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+    volatile int* s_abort = (volatile int*)(tmem_slot + 1);
+    float* s_taps = (float*)(tmem_slot + 4);  // [2][64]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cz = kz / 2;
+    const int ntiles = (nx + kN - 1) / kN;
+    const int nh = (ntiles + kTilesPerItem - 1) / kTilesPerItem;
+    const int nm = (nf + kM - 1) / kM;
+    const int total = nz * nm * nh;
+    const int it_begin = (int)((long long)blockIdx.x * total / gridDim.x);
+    const int it_end = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < gemm2::kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&b_full[s], gemm2::kBuilders);
+            mbar_init(&b_empty[s], 1);
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+        }
+        *s_abort = 0;
+        fence_barrier_init();
+        prefetch_tensormap(&tmap_in);
+        prefetch_tensormap(&tmap_out);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            int issued = 0;
+            bool stop = false;
+            for (int it = it_begin; it < it_end && !stop; ++it) {
+                const Item I = decode(it, nh, nm, ntiles);
+                int lo, hi;
+                u_range2d(I.z, kz, nz, adjoint, lo, hi);
+                for (int u = lo; u <= hi && !stop; ++u) {
+                    const int j = adjoint ? I.z + u - cz : I.z - u + cz;
+                    for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                        if (!mbar_wait_or_abort(&empty[st], ph ^ 1, s_abort, &g_wait_error,
+                                                kWaitEmpty)) {
+                            stop = true;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[st], kChunkBytes);
+                        tma_load_3d(sA + st * kChunkBytes, &tmap_in, &full[st], kKC * c - 32, j,
+                                    I.m0);
+                        if (++st == (uint32_t)gemm2::kStages) { st = 0; ph ^= 1; }
+                        ++issued;
+                    }
+                }
+            }
+            if (*s_abort) {
+                // let issued copies land before shared memory is released
+                for (int q = 0; q < min(issued, gemm2::kStages); ++q) {
+                    st = (st == 0) ? gemm2::kStages - 1 : st - 1;
+                    if (st == (uint32_t)gemm2::kStages - 1) ph ^= 1;
+                    mbar_wait(&full[st], ph, &g_wait_error, kWaitDrain);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // --------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            int step = 0, k = 0;
+            bool stop = false;
+            for (int it = it_begin; it < it_end && !stop; ++it, ++k) {
+                const Item I = decode(it, nh, nm, ntiles);
+                int lo, hi;
+                u_range2d(I.z, kz, nz, adjoint, lo, hi);
+                const int ab = k & 1;
+                if (!mbar_wait_or_abort(&acc_empty[ab], ((k >> 1) & 1) ^ 1, s_abort, &g_wait_error,
+                                        kWaitAccFree))
+                    break;
+                tc_fence_after();
+                for (int u = lo; u <= hi && !stop; ++u, ++step) {
+                    const int b = step & 1;
+                    if (!mbar_wait_or_abort(&b_full[b], (step >> 1) & 1, s_abort, &g_wait_error,
+                                            kWaitB)) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint8_t* bt = sB + (size_t)b * 3 * kBTileBytes;
+                    for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                        if (!mbar_wait_or_abort(&full[st], ph, s_abort, &g_wait_error, kWaitFull)) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a = smem_u32(sA + st * kChunkBytes);
+                        int tl[2], cp[2], np = 0;
+                        if ((c & 1) == 0 && c / 2 - 1 >= I.s0) { tl[np] = c / 2 - 1; cp[np] = 2; ++np; }
+                        if (c / 2 < I.s1) { tl[np] = c / 2; cp[np] = c & 1; ++np; }
+                        for (int q = 0; q < np; ++q) {
+                            const uint32_t d = tmem_base + (uint32_t)(ab * kAccCols) +
+                                               (uint32_t)((tl[q] - I.s0) * kN);
+                            const uint32_t bh = smem_u32(bt + cp[q] * kBTileBytes);
+#pragma unroll
+                            for (int kk = 0; kk < kKC / 16; ++kk)
+                                mma_f16(d, desc_sw128_kmajor(a) + 2 * kk,
+                                        desc_sw128_kmajor(bh) + 2 * kk, kIdesc,
+                                        (u > lo || cp[q] > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(&empty[st]);
+                        if (++st == (uint32_t)gemm2::kStages) { st = 0; ph ^= 1; }
+                    }
+                    mma_commit(&b_empty[b]);
+                }
+                if (stop) break;
+                mma_commit(&acc_full[ab]);
+            }
+        }
+        __syncwarp();
+    } else if (warp < 6) {
+        // ------------------------------------------------------ epilogue
+        const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+        uint8_t* stage_buf = sO + (size_t)(warp - 2) * 2 * kOutTileBytes;
+        int k = 0, q = 0;
+        for (int it = it_begin; it < it_end; ++it, ++k) {
+            const Item I = decode(it, nh, nm, ntiles);
+            const int ab = k & 1;
+            if (!mbar_wait_or_abort(&acc_full[ab], (k >> 1) & 1, s_abort, &g_wait_error, kWaitAcc))
+                break;
+            tc_fence_after();
+            for (int s = I.s0; s < I.s1; ++s) {
+#pragma unroll 1
+                for (int j = 0; j < kN / 32; ++j, ++q) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                           (uint32_t)(ab * kAccCols + (s - I.s0) * kN + j * 32),
+                                       r);
+                    tmem_ld_wait();
+                    uint8_t* tile = stage_buf + (q & 1) * kOutTileBytes;
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; ++c4)
+                        *reinterpret_cast<uint4*>(tile + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                            make_uint4(r[4 * c4], r[4 * c4 + 1], r[4 * c4 + 2], r[4 * c4 + 3]);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_3d(&tmap_out, tile, s * kN + j * 32, I.z, I.m0 + quarter * 32);
+                        bulk_commit();
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+        if (lane == 0) bulk_wait<0>();
+        __syncwarp();
+    } else {
+        // ------------------------------- Toeplitz tiles of each (item, u)
+        const int bt = threadIdx.x - 6 * 32;  // 0 .. 32 * kBuilders - 1
+        constexpr int kB = 32 * gemm2::kBuilders;
+        const int center = taps / 2;
+        int step = 0;
+        bool stop = false;
+        for (int it = it_begin; it < it_end && !stop; ++it) {
+            const Item I = decode(it, nh, nm, ntiles);
+            int lo, hi;
+            u_range2d(I.z, kz, nz, adjoint, lo, hi);
+            for (int u = lo; u <= hi; ++u, ++step) {
+                const int b = step & 1;
+                const bool ok = mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
+                                                   &g_wait_error, kWaitB);
+                const int krow = adjoint ? I.z : I.z - u + cz;
+                float* tp = s_taps + b * 64;
+                if (ok && bt < 64)
+                    tp[bt] = bt < taps ? __ldg(kern + ((size_t)krow * kz + u) * taps + bt) : 0.f;
+                // the taps are in; leave together if any builder or role gave up
+                if (named_bar_or<1>(kB, !ok || *s_abort)) {
+                    stop = true;
+                    break;
+                }
+                uint8_t* dst = sB + (size_t)b * 3 * kBTileBytes;
+                for (int idx = bt; idx < 3 * kN * kKC / 2; idx += kB) {
+                    // two consecutive k per thread
+                    const int c = idx / (kN * kKC / 2), rem = idx % (kN * kKC / 2);
+                    const int n = rem / (kKC / 2), k2 = (rem % (kKC / 2)) * 2;
+                    float v[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int kk = k2 + e;
+                        const int t = adjoint ? (kk + kKC * c - n - 32 + center)
+                                              : (n - kk - kKC * c + 32 + center);
+                        v[e] = (t >= 0 && t < taps) ? tp[t] : 0.f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(dst + c * kBTileBytes + sw128_offset(n, k2)) =
+                        __floats2bfloat162_rn(v[0], v[1]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&b_full[b]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
+                        const void* in, float* out, int nf, cudaStream_t st) {
+    CUtensorMap map_in, map_out;
+    int rc = make_map_3d(&map_out, out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nz, nx, nf, 32, 32,
+                         CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    rc = make_map_3d(&map_in, in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nz, nx, nf, gemm::kKC,
+                     gemm::kM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
+    const int items = nz * ((nf + gemm::kM - 1) / gemm::kM) *
+                      ((ntiles + gemm::kTilesPerItem - 1) / gemm::kTilesPerItem);
+    const int grid = items < sm_count() ? items : sm_count();
+    cudaFuncSetAttribute(tidas_gemm2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)gemm2::kSmem);
+    tidas_gemm2d_kernel<<<grid, gemm2::kThreads, gemm2::kSmem, st>>>(
+        map_in, map_out, kern, kz, taps, adjoint ? 1 : 0, nz, nx, nf);
+    return check_launch("tidas_gemm2d_kernel");
 }
 
 }  // namespace tidas

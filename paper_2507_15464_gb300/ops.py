@@ -130,6 +130,12 @@ class DasPlan:
         capi.tidas_fit_kernels(self.handle, taps, ref_stride, _ptr(k), _ptr(th), _stream())
         return k, th
 
+    def fit_kernels_2d(self, kz, taps, device="cuda"):
+        """2D band kernels [nz, kz, taps]: the image of a unit scatterer on each row."""
+        k = torch.empty((self.nz, kz, taps), dtype=torch.float32, device=device)
+        capi.tidas_fit_kernels_2d(self.handle, kz, taps, _ptr(k), _stream())
+        return k
+
 
 def _tidas(fn, kernels, x, variant, out=None):
     nz, taps = kernels.shape
@@ -152,3 +158,26 @@ def tidas_forward(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
 
 def tidas_adjoint(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
     return _tidas(capi.tidas_adjoint, kernels, img, variant, out)
+
+
+def _tidas2d(fn, kernels, x, variant, out=None):
+    nz, kz, taps = kernels.shape
+    nf, nz2, nx = x.shape
+    if nz2 != nz:
+        raise ValueError("kernel rows and image rows differ")
+    _need(kernels, torch.float32, (nz, kz, taps), "kernels")
+    want = torch.bfloat16 if variant == capi.VARIANT_GEMM_BF16 else torch.float32
+    _need(x, want, (nf, nz, nx), "input")
+    out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
+                                                  device=x.device)
+    fn(_ptr(kernels), kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
+    return out
+
+
+def tidas_forward_2d(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
+    """Eq. (2.13) with 2D band kernels: refl [B, nz, nx] -> img [B, nz, nx]."""
+    return _tidas2d(capi.tidas_forward_2d, kernels, refl, variant, out)
+
+
+def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
+    return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out)

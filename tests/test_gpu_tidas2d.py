@@ -1,0 +1,194 @@
+"""GPU parity of tiDAS with 2D band kernels (axial x lateral single-scatterer
+images per depth row, Eq. (2.13) with the axial dimension kept) against the
+FP64 oracle, through the C ABI: the kernel fit, the forward map and its
+transpose.
+
+Tolerances (relative L2 against the oracle on identical input values): kernel
+fit and direct FP32 1e-5; BF16 Toeplitz GEMM 5e-3 (BF16 rounding of the
+kernels, unit roundoff 2^-8, FP32 accumulation); adjoint identity 1e-6 with
+FP64 dot products.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from tidas_workloads import generators, presets
+
+from .gpu_helpers import dot_test, host, rel_l2, require_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 5e-3}
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def ops():
+    from paper_2507_15464_gb300 import ops as o
+    return o
+
+
+def _inputs(nf, nz, nx, kz, taps, seed):
+    refl = generators.bernoulli_normal((nf, nz, nx), 0.02 if nz * nx >= 4096 else 0.3, (seed,))
+    kern = generators.standard_normal((nz, kz, taps), (seed, 2), np.float32)
+    return refl, kern
+
+
+def _run(variant, kern, x, adjoint=False):
+    o = ops()
+    d = to_dev(x)
+    if variant == 1:
+        d = d.to(torch.bfloat16)
+    fn = o.tidas_adjoint_2d if adjoint else o.tidas_forward_2d
+    return host(fn(to_dev(kern), d, variant=variant)), (
+        host(d) if variant == 1 else x.astype(np.float64))
+
+
+def _gemm_ok(nx, taps):
+    return nx % 8 == 0 and taps <= 63
+
+
+# (frames, rows, columns, kz, taps): ragged column tiles, more than 128 frames
+# (two frame tiles), kz larger than the grid, even and odd kz, one tap
+SHAPES = [(3, 40, 512, 9, 63), (5, 17, 200, 5, 31), (2, 9, 64, 1, 4), (1, 3, 24, 7, 1),
+          (6, 5, 1500, 3, 63), (9, 4, 96, 4, 100), (2, 12, 2048, 16, 33),
+          (130, 6, 136, 5, 17)]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tidas2d_forward_matches_oracle(variant, shape):
+    import oracle
+    nf, nz, nx, kz, taps = shape
+    if variant and not _gemm_ok(nx, taps):
+        pytest.skip("the GEMM variant needs nx % 8 == 0 and taps <= 63")
+    refl, kern = _inputs(nf, nz, nx, kz, taps, 40)
+    y, x_used = _run(variant, kern, refl)
+    assert rel_l2(y, oracle.tidas_conv2d(kern, x_used)) <= TOL[variant]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("shape", [(3, 33, 256, 16, 63), (2, 7, 40, 3, 5), (130, 5, 64, 6, 9)])
+def test_tidas2d_adjoint_matches_oracle_and_identity(variant, shape):
+    import oracle
+    nf, nz, nx, kz, taps = shape
+    refl, kern = _inputs(nf, nz, nx, kz, taps, 41)
+    img = generators.standard_normal((nf, nz, nx), (42,), np.float32)
+    r, y_used = _run(variant, kern, img, adjoint=True)
+    assert rel_l2(r, oracle.tidas_conv2d_adjoint(kern, y_used)) <= TOL[variant]
+    if variant == 0:
+        hx, _ = _run(0, kern, refl)
+        dot_test(hx, img, refl, r)
+
+
+def _oracle_rows(kern, x, rows, adjoint):
+    """Oracle values of the output rows `rows` from the slab of rows they
+    depend on (every other row of that slab's band is outside the grid)."""
+    import oracle
+    nz, kz, _ = kern.shape
+    cz = kz // 2
+    out = []
+    for i in rows:
+        if adjoint:
+            lo, hi = max(0, i - cz), min(nz - 1, i + kz - 1 - cz)
+            y = oracle.tidas_conv2d_adjoint(kern[lo:hi + 1], x[:, lo:hi + 1])
+        else:
+            lo, hi = max(0, i - (kz - 1) + cz), min(nz - 1, i + cz)
+            y = oracle.tidas_conv2d(kern[lo:hi + 1], x[:, lo:hi + 1])
+        out.append(y[:, i - lo])
+    return np.stack(out, axis=1)
+
+
+@functools.lru_cache(maxsize=1)
+def _full_size_inputs():
+    # 256 frames of 1024 x 512 maps with 16 x 63 band kernels
+    nf, nz, nx, kz, taps = 256, 1024, 512, 16, 63
+    x = np.empty((nf, nz, nx), np.float32)
+    for f in range(nf):
+        x[f] = generators.bernoulli_normal((nz, nx), 0.02, (2, f))
+    return x, generators.standard_normal((nz, kz, taps), (43,), np.float32)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_tidas2d_full_size_sampled_rows(variant, adjoint):
+    x, kern = _full_size_inputs()
+    y, x_used = _run(variant, kern, x, adjoint)
+    rows = [0, 1, 7, 511, 1016, 1022, 1023]
+    frames = np.array([0, 127, 128, 255])
+    ref = _oracle_rows(kern, x_used[frames], rows, adjoint)
+    assert rel_l2(y[frames][:, rows], ref) <= TOL[variant]
+
+
+# ------------------------------------------------------------- kernel fit
+def test_fit_kernels_2d_matches_oracle_patches():
+    import oracle as orc
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = presets.geometry("pw64_single")
+    P = DasPlan(g)
+    kz, taps = 9, 31
+    k = host(P.fit_kernels_2d(kz, taps))
+    assert k.shape == (g["nz"], kz, taps)
+    rows = [0, 1, 100, g["nz"] - 1]
+    ref = orc.Oracle(g).psf_patches(kz, taps, rows=rows)
+    assert rel_l2(k[rows], ref) <= TOL32
+
+
+def test_fit_kernels_2d_centre_slice_is_the_row_kernel():
+    # kz = 1 and the centre slice of any kz evaluate the same pixels
+    from paper_2507_15464_gb300.ops import DasPlan
+    P = DasPlan(presets.geometry("pw64_single"))
+    k1, _ = P.fit_kernels(31)
+    k2 = P.fit_kernels_2d(16, 31)
+    assert torch.equal(k2[:, 8, :], k1)
+    assert torch.equal(P.fit_kernels_2d(1, 31)[:, 0, :], k1)
+
+
+def test_fit_kernels_2d_compound_sampled_rows():
+    import oracle as orc
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = presets.geometry("pw128_compound")
+    k = host(DasPlan(g).fit_kernels_2d(16, 63))
+    rows = [0, 517, 1023]
+    ref = orc.Oracle(g).psf_patches(16, 63, rows=rows)
+    assert rel_l2(k[rows], ref) <= TOL32
+
+
+def test_band_kernel_reproduces_das_of_its_scatterer():
+    # Sections 2.2-2.3 with the axial extent kept: a unit scatterer on the
+    # fitting pixel (ic, j) maps to its exact DAS image inside the kz x taps
+    # window, and to zero outside it
+    o = ops()
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = presets.geometry("pw64_single")
+    P = DasPlan(g)
+    kz, taps, j, ic = 15, 31, 100, g["nx"] // 2
+    refl = torch.zeros((1, g["nz"], g["nx"]), device="cuda")
+    refl[0, j, ic] = 1.0
+    das = host(P.forward(P.synthesize_grid(refl)))[0]
+    y = host(o.tidas_forward_2d(P.fit_kernels_2d(kz, taps), refl))[0]
+    rows = slice(j - kz // 2, j - kz // 2 + kz)
+    cols = slice(ic - taps // 2, ic - taps // 2 + taps)
+    assert rel_l2(y[rows, cols], das[rows, cols]) <= 1e-4
+    y[rows, cols] = 0.0
+    assert not y.any()
+
+
+def test_band_kernels_are_closer_to_exact_das_than_row_kernels():
+    # the band keeps the PSF's axial extent that the lateral kernels drop; the
+    # lateral shift variance of the PSF bounds both (0.37 -> 0.33 on this map)
+    o = ops()
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = presets.geometry("pw64_single")
+    P = DasPlan(g)
+    refl = to_dev(generators.bernoulli_normal((1, g["nz"], g["nx"]), 0.02, (44,)))
+    das = P.forward(P.synthesize_grid(refl)).double()
+    k1, _ = P.fit_kernels(31)
+    e1 = (o.tidas_forward(k1, refl).double() - das).norm() / das.norm()
+    e2 = (o.tidas_forward_2d(P.fit_kernels_2d(31, 31), refl).double() - das).norm() / das.norm()
+    assert float(e2) < float(e1), (float(e1), float(e2))
