@@ -199,13 +199,22 @@ int tidas_fit_kernels_2d(das_plan plan, int32_t kz, int32_t taps, float* kernels
  * tidas_adjoint_2d is the transpose.  variant: TIDAS_VARIANT_DIRECT (FP32
  * CUDA cores, refl float32) or TIDAS_VARIANT_GEMM_BF16 (tcgen05 Toeplitz
  * GEMMs over the kz input rows; refl BF16, taps <= 63, nx % 8 == 0, 16-byte
- * aligned arrays).  nx <= 2048. */
+ * aligned arrays).  nx <= 2048.
+ * workspace: device scratch of at least tidas_band_workspace_bytes(nz, nx,
+ * n_frames, variant) bytes, 16-byte aligned, owned by the caller and not
+ * read or written by any other work on the stream until the call's kernels
+ * end; NULL makes the call take it from the stream-ordered allocator and
+ * release it after its kernels (0 bytes are needed by the direct variant). */
 int tidas_forward_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz, int32_t nx,
                      const void* refl, float* img, int32_t n_frames, int32_t variant,
-                     void* stream);
+                     void* workspace, size_t workspace_bytes, void* stream);
 int tidas_adjoint_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz, int32_t nx,
                      const void* img, float* refl, int32_t n_frames, int32_t variant,
-                     void* stream);
+                     void* workspace, size_t workspace_bytes, void* stream);
+/* Scratch bytes of the 2D band calls: the input repacked into the GEMM's
+ * operand tiles (128 frames x 64 columns, 16 KB each, per row); 0 for
+ * variants that need none or for invalid sizes. */
+size_t tidas_band_workspace_bytes(int32_t nz, int32_t nx, int32_t n_frames, int32_t variant);
 
 /* ------------------------------------------------------------------------
  * Deconvolution on the convolutional model (the use the paper names for it in

@@ -36,6 +36,7 @@ class das_params(ctypes.Structure):
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
+_S = ctypes.c_size_t
 _SIG = {
     "das_plan_create": [ctypes.POINTER(das_params), ctypes.POINTER(ctypes.c_void_p)],
     "das_plan_destroy": [_P],
@@ -69,12 +70,14 @@ _SIG = {
     "tidas_encode": [_P, _I, _P, _P, _P, _P],
     "tidas_mlp_infer": [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _I, _P],
     "tidas_fit_kernels_2d": [_P, _I, _I, _P, _P],
-    "tidas_forward_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P],
-    "tidas_adjoint_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P],
+    "tidas_forward_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _S, _P],
+    "tidas_adjoint_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _S, _P],
     "tidas_forward_varying": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
     "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
     "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],
+    "tidas_band_workspace_bytes": [_I, _I, _I, _I],
 }
+_RESTYPE = {"tidas_band_workspace_bytes": _S}
 EXPORTED = list(_SIG) + ["tidas_last_error"]
 
 _lib = None
@@ -98,7 +101,7 @@ def load(build_if_missing=True):
     for name, args in _SIG.items():
         f = getattr(L, name)
         f.argtypes = args
-        f.restype = ctypes.c_int
+        f.restype = _RESTYPE.get(name, ctypes.c_int)
     L.tidas_last_error.argtypes = []
     L.tidas_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -162,14 +165,20 @@ def tidas_fit_kernels_2d(plan, kz, taps, kernels, stream=0):
     return _check(load().tidas_fit_kernels_2d(plan, kz, taps, kernels, stream))
 
 
-def tidas_forward_2d(kernels, kz, taps, nz, nx, refl, img, n_frames, variant, stream=0):
+def tidas_forward_2d(kernels, kz, taps, nz, nx, refl, img, n_frames, variant, workspace=None,
+                     workspace_bytes=0, stream=0):
     return _check(load().tidas_forward_2d(kernels, kz, taps, nz, nx, refl, img, n_frames, variant,
-                                          stream))
+                                          workspace, workspace_bytes, stream))
 
 
-def tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant, stream=0):
+def tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant, workspace=None,
+                     workspace_bytes=0, stream=0):
     return _check(load().tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant,
-                                          stream))
+                                          workspace, workspace_bytes, stream))
+
+
+def tidas_band_workspace_bytes(nz, nx, n_frames, variant):
+    return load().tidas_band_workspace_bytes(nz, nx, n_frames, variant)
 
 
 def tidas_dot(a, b, n, out, stream=0):

@@ -9,7 +9,9 @@ int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int
 int launch_tidas_direct2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
                           const float* in, float* out, int nf, cudaStream_t st);
 int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
-                        const void* in, float* out, int nf, cudaStream_t st);
+                        const void* in, float* out, int nf, void* workspace, size_t ws_bytes,
+                        cudaStream_t st);
+size_t band_pack_bytes(int nz, int nx, int nf);
 int launch_fit_kernels_2d(const Plan& P, int kz, int taps, float* kernels, cudaStream_t st);
 }  // namespace tidas
 
@@ -132,9 +134,16 @@ extern "C" int tidas_fit_kernels_2d(das_plan plan, int32_t kz, int32_t taps, flo
     return launch_fit_kernels_2d(P, kz, taps, kernels, S_(stream));
 }
 
+extern "C" size_t tidas_band_workspace_bytes(int32_t nz, int32_t nx, int32_t n_frames,
+                                            int32_t variant) {
+    if (variant != TIDAS_VARIANT_GEMM_BF16 || nz < 1 || nx < 1 || n_frames < 1) return 0;
+    return band_pack_bytes(nz, nx, n_frames);
+}
+
 static int tidas2d_common(const char* who, const float* kernels, int32_t kz, int32_t taps,
                           int32_t nz, int32_t nx, const void* in, float* out, int32_t n_frames,
-                          int32_t variant, bool adjoint, void* stream) {
+                          int32_t variant, void* workspace, size_t ws_bytes, bool adjoint,
+                          void* stream) {
     TIDAS_REQUIRE(kernels && in && out, "%s: null pointer", who);
     TIDAS_REQUIRE(taps >= 1 && taps <= 255 && kz >= 1 && kz <= 64, "%s: bad kernel shape", who);
     TIDAS_REQUIRE(nz >= 1 && nz <= 65535 && nx >= 1 && nx <= 2048, "%s: bad grid", who);
@@ -148,7 +157,7 @@ static int tidas2d_common(const char* who, const float* kernels, int32_t kz, int
         TIDAS_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0,
                       "%s: the GEMM variant needs 16-byte aligned arrays", who);
         return launch_tidas_gemm2d(kernels, kz, taps, adjoint, nz, nx, in, out, n_frames,
-                                   S_(stream));
+                                   workspace, ws_bytes, S_(stream));
     }
     return set_error(TIDAS_ERR_ARG, "%s: variant %d is not available for 2D kernels", who,
                      variant);
@@ -156,14 +165,16 @@ static int tidas2d_common(const char* who, const float* kernels, int32_t kz, int
 
 extern "C" int tidas_forward_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz,
                                 int32_t nx, const void* refl, float* img, int32_t n_frames,
-                                int32_t variant, void* stream) {
+                                int32_t variant, void* workspace, size_t workspace_bytes,
+                                void* stream) {
     return tidas2d_common("tidas_forward_2d", kernels, kz, taps, nz, nx, refl, img, n_frames,
-                          variant, false, stream);
+                          variant, workspace, workspace_bytes, false, stream);
 }
 
 extern "C" int tidas_adjoint_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz,
                                 int32_t nx, const void* img, float* refl, int32_t n_frames,
-                                int32_t variant, void* stream) {
+                                int32_t variant, void* workspace, size_t workspace_bytes,
+                                void* stream) {
     return tidas2d_common("tidas_adjoint_2d", kernels, kz, taps, nz, nx, img, refl, n_frames,
-                          variant, true, stream);
+                          variant, workspace, workspace_bytes, true, stream);
 }

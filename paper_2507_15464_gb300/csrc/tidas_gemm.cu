@@ -467,20 +467,72 @@ int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int
 // ------------------------------------------------- 2D band kernels (tcgen05)
 // Y_z = sum_u R_{j(u)} T_{j(u), u}: the row-wise Toeplitz GEMM summed over the
 // kz input rows j = z - u + kz/2 (adjoint: j = z + u - kz/2, kernel row z)
-// into the same accumulators.  A step = (item, u): the producer streams the
-// item's input chunks of row j, six builder warps write that step's three
-// Toeplitz tiles (double buffered), the MMA warp issues the item's MMAs.
+// into the same accumulators.  A step = (item, u): the producer copies the
+// item's input chunks of row j, six builder warps write that step's band
+// matrix (double buffered), the MMA warp issues the item's MMAs.
+//
+// The input is first repacked into the operand's shared-memory image: chunk q
+// of (row z, frame tile m) holds columns [64 q - 32, 64 q + 32) of 128 frames
+// as a 16 KB 128-byte-swizzled K-major tile, zero outside the grid, so that
+// the producer moves two neighbouring chunks (a 32 KB stage) with one
+// contiguous bulk copy.  A tiled tensor copy moves a 128-byte row at a time,
+// and the issuing thread of the MMAs pays a barrier wait and a commit per
+// stage while the tensor pipe, whose queue holds about one MMA, runs dry:
+// stages of 2 chunks (3 per step instead of 5) keep it fed.
 namespace gemm2 {
-constexpr int kStages = 4;
-constexpr int kBBufs = 2;
+constexpr int kStages = 3;
+constexpr int kStageBytes = 2 * gemm::kChunkBytes;  // two 64-column chunks
 constexpr int kBuilders = 6;  // warps 6 .. 11
 constexpr int kThreads = 32 * (6 + kBuilders);
+// The three Toeplitz tiles of a step (part cp = 0, 1, 2 of a tile's three
+// input chunks) are windows of one band matrix G[r][k], r in [-128, 128):
+// tile cp, row n = G row n - 64 cp.  G is 256 rows of 128 bytes (SW128).
+constexpr int kGRows = 256;
+constexpr int kGBytes = kGRows * 128;
+// G rows are 16-byte copies out of 8 phase-shifted BF16 copies of the
+// step's kernel slice, s_p[m] = s(m + p), m < kRevLen
+constexpr int kRevLen = 192;
 constexpr size_t kOffA = 0;
-constexpr size_t kOffB = kOffA + (size_t)kStages * gemm::kChunkBytes;
-constexpr size_t kOffO = kOffB + (size_t)kBBufs * 3 * gemm::kBTileBytes;
-constexpr size_t kOffBar = kOffO + (size_t)4 * 2 * gemm::kOutTileBytes;
-constexpr size_t kSmem = 1024 + kOffBar + 1024;
+constexpr size_t kOffB = kOffA + (size_t)kStages * kStageBytes;
+constexpr size_t kOffO = kOffB + (size_t)2 * kGBytes;
+constexpr size_t kOffRev = kOffO + (size_t)4 * 2 * gemm::kOutTileBytes;
+constexpr size_t kOffBar = kOffRev + (size_t)2 * 8 * kRevLen * 2;
+constexpr size_t kSmem = 1024 + kOffBar + 256;
+static_assert(kSmem <= 227 * 1024, "shared memory");
+
+// chunks per (row, frame tile): 2 per column tile, one for the right halo and
+// one zero chunk so that every stage is a whole chunk pair
+__host__ __device__ inline int n_chunks(int nx) {
+    return 2 * ((nx + gemm::kN - 1) / gemm::kN) + 2;
+}
 }  // namespace gemm2
+
+size_t band_pack_bytes(int nz, int nx, int nf) {
+    return (size_t)nz * ((nf + gemm::kM - 1) / gemm::kM) * gemm2::n_chunks(nx) * gemm::kChunkBytes;
+}
+
+// in [nf][nz][nx] BF16 -> packed [nz][nm][nq] chunk images; one thread per
+// 16-byte piece (8 columns of one frame)
+__global__ void tidas_band_pack_kernel(const __nv_bfloat16* __restrict__ in,
+                                       uint8_t* __restrict__ packed, int nz, int nx, int nf,
+                                       int nm, int nq) {
+    const size_t total = (size_t)nz * nm * nq * gemm::kM * 8;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i & 7);
+        const int f = (int)((i >> 3) % gemm::kM);
+        const size_t t = (i >> 3) / gemm::kM;  // (z * nm + m) * nq + q
+        const int q = (int)(t % nq);
+        const int m = (int)((t / nq) % nm);
+        const int z = (int)(t / ((size_t)nq * nm));
+        const int x0 = gemm::kKC * q - 32 + 8 * j;
+        const int fr = m * gemm::kM + f;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (fr < nf && x0 >= 0 && x0 < nx)
+            v = __ldg(reinterpret_cast<const uint4*>(in + ((size_t)fr * nz + z) * nx + x0));
+        *reinterpret_cast<uint4*>(packed + t * gemm::kChunkBytes + sw128_offset(f, 8 * j)) = v;
+    }
+}
 
 __device__ __forceinline__ void u_range2d(int z, int kz, int nz, bool adjoint, int& lo, int& hi) {
     const int cz = kz / 2;
@@ -494,15 +546,16 @@ __device__ __forceinline__ void u_range2d(int z, int kz, int nz, bool adjoint, i
 }
 
 __global__ void __launch_bounds__(gemm2::kThreads, 1)
-    tidas_gemm2d_kernel(const __grid_constant__ CUtensorMap tmap_in,
+    tidas_gemm2d_kernel(const uint8_t* __restrict__ packed,
                         const __grid_constant__ CUtensorMap tmap_out, const float* __restrict__ kern,
                         int kz, int taps, int adjoint, int nz, int nx, int nf) {
     using namespace gemm;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base + gemm2::kOffA;  // [stage] BF16 input chunks
-    uint8_t* sB = base + gemm2::kOffB;  // [buf][3] Toeplitz tiles
+    uint8_t* sB = base + gemm2::kOffB;  // [buf] band matrix G
     uint8_t* sO = base + gemm2::kOffO;  // [epilogue warp][2] output staging tiles
+    __nv_bfloat16* s_rev = (__nv_bfloat16*)(base + gemm2::kOffRev);  // [buf][8][kRevLen]
     uint64_t* full = (uint64_t*)(base + gemm2::kOffBar);
     uint64_t* empty = full + gemm2::kStages;
     uint64_t* b_full = empty + gemm2::kStages;
@@ -511,16 +564,18 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
     uint64_t* acc_empty = acc_full + 2;
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
-    float* s_taps = (float*)(tmem_slot + 4);  // [2][64]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cz = kz / 2;
     const int ntiles = (nx + kN - 1) / kN;
     const int nh = (ntiles + kTilesPerItem - 1) / kTilesPerItem;
     const int nm = (nf + kM - 1) / kM;
+    const int nq = gemm2::n_chunks(nx);
     const int total = nz * nm * nh;
-    const int it_begin = (int)((long long)blockIdx.x * total / gridDim.x);
-    const int it_end = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
+    // items strided over the grid: the CTAs work on neighbouring rows at the
+    // same time, so that each input row is fetched from DRAM about once and
+    // its kz uses hit L2
+    const int it_begin = blockIdx.x, it_step = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < gemm2::kStages; ++s) {
@@ -535,7 +590,6 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
         }
         *s_abort = 0;
         fence_barrier_init();
-        prefetch_tensormap(&tmap_in);
         prefetch_tensormap(&tmap_out);
     }
     if (warp == 1) {
@@ -548,26 +602,29 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer
+        // ------------------------------------------------ bulk-copy producer
         if (lane == 0) {
             uint32_t st = 0, ph = 0;
             int issued = 0;
             bool stop = false;
-            for (int it = it_begin; it < it_end && !stop; ++it) {
+            for (int it = it_begin; it < total && !stop; it += it_step) {
                 const Item I = decode(it, nh, nm, ntiles);
                 int lo, hi;
                 u_range2d(I.z, kz, nz, adjoint, lo, hi);
                 for (int u = lo; u <= hi && !stop; ++u) {
                     const int j = adjoint ? I.z + u - cz : I.z - u + cz;
-                    for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                    const uint8_t* src =
+                        packed + ((size_t)j * nm + I.m0 / kM) * nq * (size_t)kChunkBytes;
+                    // chunk pairs (2 s0 + 2 p, + 1), p = 0 .. s1 - s0
+                    for (int c = 2 * I.s0; c <= 2 * I.s1; c += 2) {
                         if (!mbar_wait_or_abort(&empty[st], ph ^ 1, s_abort, &g_wait_error,
                                                 kWaitEmpty)) {
                             stop = true;
                             break;
                         }
-                        mbar_arrive_expect_tx(&full[st], kChunkBytes);
-                        tma_load_3d(sA + st * kChunkBytes, &tmap_in, &full[st], kKC * c - 32, j,
-                                    I.m0);
+                        mbar_arrive_expect_tx(&full[st], gemm2::kStageBytes);
+                        bulk_load(sA + st * gemm2::kStageBytes, src + (size_t)c * kChunkBytes,
+                                  gemm2::kStageBytes, &full[st]);
                         if (++st == (uint32_t)gemm2::kStages) { st = 0; ph ^= 1; }
                         ++issued;
                     }
@@ -589,7 +646,7 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
             uint32_t st = 0, ph = 0;
             int step = 0, k = 0;
             bool stop = false;
-            for (int it = it_begin; it < it_end && !stop; ++it, ++k) {
+            for (int it = it_begin; it < total && !stop; it += it_step, ++k) {
                 const Item I = decode(it, nh, nm, ntiles);
                 int lo, hi;
                 u_range2d(I.z, kz, nz, adjoint, lo, hi);
@@ -606,26 +663,33 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint8_t* bt = sB + (size_t)b * 3 * kBTileBytes;
-                    for (int c = 2 * I.s0; c <= 2 * I.s1; ++c) {
+                    const uint64_t dg = desc_sw128_kmajor(smem_u32(sB + (size_t)b * gemm2::kGBytes));
+                    for (int c2 = 2 * I.s0; c2 <= 2 * I.s1; c2 += 2) {
+                        // the bulk copy's completion on full[st] makes the
+                        // pair visible to the MMAs; no tcgen05 fence needed
                         if (!mbar_wait_or_abort(&full[st], ph, s_abort, &g_wait_error, kWaitFull)) {
                             stop = true;
                             break;
                         }
-                        tc_fence_after();
-                        const uint32_t a = smem_u32(sA + st * kChunkBytes);
-                        int tl[2], cp[2], np = 0;
-                        if ((c & 1) == 0 && c / 2 - 1 >= I.s0) { tl[np] = c / 2 - 1; cp[np] = 2; ++np; }
-                        if (c / 2 < I.s1) { tl[np] = c / 2; cp[np] = c & 1; ++np; }
-                        for (int q = 0; q < np; ++q) {
-                            const uint32_t d = tmem_base + (uint32_t)(ab * kAccCols) +
-                                               (uint32_t)((tl[q] - I.s0) * kN);
-                            const uint32_t bh = smem_u32(bt + cp[q] * kBTileBytes);
+                        // descriptors of the pair's two chunks and of the
+                        // three windows of G; a K-step adds 32 bytes (2)
+                        const uint64_t da = desc_sw128_kmajor(smem_u32(sA + st * gemm2::kStageBytes));
+                        const uint32_t acc_u = (u > lo) ? 1u : 0u;
+                        // tile tl (relative to s0) from window cp of chunk h
+                        auto tile = [&](int tl, int cp, int h) {
+                            const uint32_t d = tmem_base + (uint32_t)(ab * kAccCols) + (uint32_t)(tl * kN);
+                            const uint64_t a = da + (uint64_t)(h * (kChunkBytes >> 4));
+                            const uint64_t bb = dg + (uint64_t)((2 - cp) * (64 * 128 >> 4));
 #pragma unroll
                             for (int kk = 0; kk < kKC / 16; ++kk)
-                                mma_f16(d, desc_sw128_kmajor(a) + 2 * kk,
-                                        desc_sw128_kmajor(bh) + 2 * kk, kIdesc,
-                                        (u > lo || cp[q] > 0 || kk > 0) ? 1u : 0u);
+                                mma_f16(d, a + 2 * kk, bb + 2 * kk, kIdesc,
+                                        (kk > 0 || cp > 0) ? 1u : acc_u);
+                        };
+                        const int t0 = c2 / 2 - I.s0;  // the pair is chunks 2 (s0 + t0), + 1
+                        if (t0 > 0) tile(t0 - 1, 2, 0);
+                        if (t0 < I.s1 - I.s0) {
+                            tile(t0, 0, 0);
+                            tile(t0, 1, 1);
                         }
                         mma_commit(&empty[st]);
                         if (++st == (uint32_t)gemm2::kStages) { st = 0; ph ^= 1; }
@@ -642,7 +706,7 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
         const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
         uint8_t* stage_buf = sO + (size_t)(warp - 2) * 2 * kOutTileBytes;
         int k = 0, q = 0;
-        for (int it = it_begin; it < it_end; ++it, ++k) {
+        for (int it = it_begin; it < total; it += it_step, ++k) {
             const Item I = decode(it, nh, nm, ntiles);
             const int ab = k & 1;
             if (!mbar_wait_or_abort(&acc_full[ab], (k >> 1) & 1, s_abort, &g_wait_error, kWaitAcc))
@@ -678,49 +742,78 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
         if (lane == 0) bulk_wait<0>();
         __syncwarp();
     } else {
-        // ------------------------------- Toeplitz tiles of each (item, u)
+        // ------------------------------- band matrix G of each (item, u)
+        // G[r][k] = s(62 - r + k) with s(m) = h[94 + c - m] (forward, value
+        // h[r - k + 32 + c]) or h[m - 94 + c] (adjoint, h[k - r - 32 + c]),
+        // c = taps / 2.  Rows outside [r_lo, r_hi] are zero for every slice,
+        // and so are the phase-copy entries of s outside the taps: both are
+        // cleared once, and a step rewrites only the taps and the band rows.
         const int bt = threadIdx.x - 6 * 32;  // 0 .. 32 * kBuilders - 1
         constexpr int kB = 32 * gemm2::kBuilders;
         const int center = taps / 2;
-        int step = 0;
-        bool stop = false;
-        for (int it = it_begin; it < it_end && !stop; ++it) {
-            const Item I = decode(it, nh, nm, ntiles);
-            int lo, hi;
-            u_range2d(I.z, kz, nz, adjoint, lo, hi);
-            for (int u = lo; u <= hi; ++u, ++step) {
-                const int b = step & 1;
-                const bool ok = mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
-                                                   &g_wait_error, kWaitB);
-                const int krow = adjoint ? I.z : I.z - u + cz;
-                float* tp = s_taps + b * 64;
-                if (ok && bt < 64)
-                    tp[bt] = bt < taps ? __ldg(kern + ((size_t)krow * kz + u) * taps + bt) : 0.f;
-                // the taps are in; leave together if any builder or role gave up
-                if (named_bar_or<1>(kB, !ok || *s_abort)) {
-                    stop = true;
-                    break;
-                }
-                uint8_t* dst = sB + (size_t)b * 3 * kBTileBytes;
-                for (int idx = bt; idx < 3 * kN * kKC / 2; idx += kB) {
-                    // two consecutive k per thread
-                    const int c = idx / (kN * kKC / 2), rem = idx % (kN * kKC / 2);
-                    const int n = rem / (kKC / 2), k2 = (rem % (kKC / 2)) * 2;
-                    float v[2];
+        const int r_lo = adjoint ? center - 31 - taps : -32 - center;
+        const int r_hi = adjoint ? 31 + center : 30 - center + taps;
+        const int n_rows = r_hi - r_lo + 1;
+        for (int idx = bt; idx < 2 * gemm2::kGRows * 8; idx += kB) {
+            const int b = idx / (gemm2::kGRows * 8), row = (idx / 8) % gemm2::kGRows;
+            const int r = row - 128;
+            if (r < r_lo || r > r_hi)
+                *reinterpret_cast<uint4*>(sB + (size_t)b * gemm2::kGBytes + row * 128 +
+                                          (idx % 8) * 16) = make_uint4(0, 0, 0, 0);
+        }
+        for (int idx = bt; idx < 2 * 8 * gemm2::kRevLen / 2; idx += kB)
+            reinterpret_cast<uint32_t*>(s_rev)[idx] = 0u;
+        // tap bt of a slice sits at s index m_t, i.e. at m_t - p in copy p
+        const int m_t = adjoint ? bt + 94 - center : 94 + center - bt;
+        named_bar_sync<1>(kB);
+        // the slice value this thread carries into the next step
+        auto slice_tap = [&](int it, int u) -> float {
+            if (bt >= taps || it >= total) return 0.f;
+            const int z = it / (nh * nm);
+            const int krow = adjoint ? z : z - u + cz;
+            return __ldg(kern + ((size_t)krow * kz + u) * taps + bt);
+        };
+        int it = it_begin, lo = 0, hi = -1, u = 0;
+        if (it < total) {
+            u_range2d(decode(it, nh, nm, ntiles).z, kz, nz, adjoint, lo, hi);
+            u = lo;
+        }
+        float tap = slice_tap(it, u);
+        for (int step = 0; it < total; ++step) {
+            const int b = step & 1;
+            const bool ok = mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
+                                               &g_wait_error, kWaitB);
+            __nv_bfloat16* rev = s_rev + b * 8 * gemm2::kRevLen;
+            if (ok && bt < taps) {
+                const __nv_bfloat16 hv = __float2bfloat16_rn(tap);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int kk = k2 + e;
-                        const int t = adjoint ? (kk + kKC * c - n - 32 + center)
-                                              : (n - kk - kKC * c + 32 + center);
-                        v[e] = (t >= 0 && t < taps) ? tp[t] : 0.f;
-                    }
-                    *reinterpret_cast<__nv_bfloat162*>(dst + c * kBTileBytes + sw128_offset(n, k2)) =
-                        __floats2bfloat162_rn(v[0], v[1]);
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&b_full[b]);
+                for (int p = 0; p < 8; ++p) rev[p * gemm2::kRevLen + m_t - p] = hv;
             }
+            // the taps are in; leave together if any builder or role gave up
+            if (named_bar_or<1>(kB, !ok || *s_abort)) break;
+            // next step's slice, loaded while this one is built
+            if (u < hi) {
+                ++u;
+            } else {
+                it += it_step;
+                if (it < total) {
+                    u_range2d(decode(it, nh, nm, ntiles).z, kz, nz, adjoint, lo, hi);
+                    u = lo;
+                }
+            }
+            tap = slice_tap(it, u);
+            uint8_t* dst = sB + (size_t)b * gemm2::kGBytes;
+            for (int idx = bt; idx < n_rows * 8; idx += kB) {
+                const int r = r_lo + idx / 8, j = idx % 8;
+                const int m0 = 62 - r + 8 * j;  // 0 .. 181
+                const uint4 v = *reinterpret_cast<const uint4*>(
+                    rev + (m0 & 7) * gemm2::kRevLen + (m0 & ~7));
+                const int row = r + 128;
+                *reinterpret_cast<uint4*>(dst + row * 128 + ((j ^ (row & 7)) << 4)) = v;
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&b_full[b]);
         }
     }
     tc_fence_before();
@@ -732,23 +825,41 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
 }
 
 int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int nz, int nx,
-                        const void* in, float* out, int nf, cudaStream_t st) {
-    CUtensorMap map_in, map_out;
+                        const void* in, float* out, int nf, void* workspace, size_t ws_bytes,
+                        cudaStream_t st) {
+    CUtensorMap map_out;
     int rc = make_map_3d(&map_out, out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nz, nx, nf, 32, 32,
                          CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
-    rc = make_map_3d(&map_in, in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, nz, nx, nf, gemm::kKC,
-                     gemm::kM, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (rc) return rc;
-    const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
-    const int items = nz * ((nf + gemm::kM - 1) / gemm::kM) *
-                      ((ntiles + gemm::kTilesPerItem - 1) / gemm::kTilesPerItem);
-    const int grid = items < sm_count() ? items : sm_count();
-    cudaFuncSetAttribute(tidas_gemm2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)gemm2::kSmem);
-    tidas_gemm2d_kernel<<<grid, gemm2::kThreads, gemm2::kSmem, st>>>(
-        map_in, map_out, kern, kz, taps, adjoint ? 1 : 0, nz, nx, nf);
-    return check_launch("tidas_gemm2d_kernel");
+    const size_t need = band_pack_bytes(nz, nx, nf);
+    uint8_t* packed = (uint8_t*)workspace;
+    if (packed) {
+        if (ws_bytes < need)
+            return set_error(TIDAS_ERR_ARG, "tidas 2D GEMM: workspace of %zu bytes, need %zu",
+                             ws_bytes, need);
+        if ((uintptr_t)packed % 16)
+            return set_error(TIDAS_ERR_ARG, "tidas 2D GEMM: workspace must be 16-byte aligned");
+    } else {
+        TIDAS_CUDA(cudaMallocAsync((void**)&packed, need, st));
+    }
+    const int nm = (nf + gemm::kM - 1) / gemm::kM, nq = gemm2::n_chunks(nx);
+    const size_t pieces = (size_t)nz * nm * nq * gemm::kM * 8;
+    const int pgrid = (int)std::min<size_t>((pieces + 255) / 256, (size_t)sm_count() * 16);
+    tidas_band_pack_kernel<<<pgrid, 256, 0, st>>>((const __nv_bfloat16*)in, packed, nz, nx, nf,
+                                                  nm, nq);
+    rc = check_launch("tidas_band_pack_kernel");
+    if (rc == TIDAS_OK) {
+        const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
+        const int items = nz * nm * ((ntiles + gemm::kTilesPerItem - 1) / gemm::kTilesPerItem);
+        const int grid = items < sm_count() ? items : sm_count();
+        cudaFuncSetAttribute(tidas_gemm2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemm2::kSmem);
+        tidas_gemm2d_kernel<<<grid, gemm2::kThreads, gemm2::kSmem, st>>>(
+            packed, map_out, kern, kz, taps, adjoint ? 1 : 0, nz, nx, nf);
+        rc = check_launch("tidas_gemm2d_kernel");
+    }
+    if (!workspace) cudaFreeAsync(packed, st);
+    return rc;
 }
 
 }  // namespace tidas

@@ -160,7 +160,7 @@ def tidas_adjoint(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
     return _tidas(capi.tidas_adjoint, kernels, img, variant, out)
 
 
-def _tidas2d(fn, kernels, x, variant, out=None):
+def _tidas2d(fn, kernels, x, variant, out=None, workspace=None):
     nz, kz, taps = kernels.shape
     nf, nz2, nx = x.shape
     if nz2 != nz:
@@ -170,14 +170,23 @@ def _tidas2d(fn, kernels, x, variant, out=None):
     _need(x, want, (nf, nz, nx), "input")
     out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
                                                   device=x.device)
-    fn(_ptr(kernels), kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
+    ws, wsb = None, 0
+    if workspace is not None:
+        ws, wsb = _ptr(workspace), workspace.numel() * workspace.element_size()
+    fn(_ptr(kernels), kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, ws, wsb, _stream())
     return out
 
 
-def tidas_forward_2d(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
+def band_workspace(nz, nx, n_frames, variant, device="cuda"):
+    """Scratch for the 2D band calls (None when the variant needs none)."""
+    n = capi.tidas_band_workspace_bytes(nz, nx, n_frames, variant)
+    return torch.empty((n,), dtype=torch.uint8, device=device) if n else None
+
+
+def tidas_forward_2d(kernels, refl, variant=capi.VARIANT_DIRECT, out=None, workspace=None):
     """Eq. (2.13) with 2D band kernels: refl [B, nz, nx] -> img [B, nz, nx]."""
-    return _tidas2d(capi.tidas_forward_2d, kernels, refl, variant, out)
+    return _tidas2d(capi.tidas_forward_2d, kernels, refl, variant, out, workspace)
 
 
-def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
-    return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out)
+def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None, workspace=None):
+    return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out, workspace)

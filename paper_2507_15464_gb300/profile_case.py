@@ -2,6 +2,7 @@
 
 python -m paper_2507_15464_gb300.profile_case das --frames 8 --dtype f16 --iters 3
 python -m paper_2507_15464_gb300.profile_case tidas --variant 1 --frames 64 --iters 3
+python -m paper_2507_15464_gb300.profile_case tidas2d --variant 1 --kz 16 --frames 256 --iters 3
 
 Inputs are seeded random arrays of the benchmark's shapes (the kernels'
 cost does not depend on the values); nothing is checked here.
@@ -16,11 +17,13 @@ sys.path.insert(0, ROOT)
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["das", "das_adjoint", "tidas", "tidas_adjoint"])
+    ap.add_argument("case", choices=["das", "das_adjoint", "tidas", "tidas_adjoint", "tidas2d",
+                                        "tidas2d_adjoint"])
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--dtype", default="f16", choices=["f16", "f32"])
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--kz", type=int, default=16)
     ap.add_argument("--geom", default="pw128_compound")
     a = ap.parse_args()
 
@@ -40,11 +43,15 @@ def main():
             fn = lambda: P.adjoint(x)
     else:
         nz, nx = g["nz"], g["nx"]
-        k = torch.randn((nz, 63), device="cuda", generator=gen)
+        band = a.case.startswith("tidas2d")
+        k = torch.randn((nz, a.kz, 63) if band else (nz, 63), device="cuda", generator=gen)
         x = torch.randn((a.frames, nz, nx), device="cuda", generator=gen)
         if a.variant == 1:
             x = x.to(torch.bfloat16)
-        f = ops.tidas_forward if a.case == "tidas" else ops.tidas_adjoint
+        if band:
+            f = ops.tidas_forward_2d if a.case == "tidas2d" else ops.tidas_adjoint_2d
+        else:
+            f = ops.tidas_forward if a.case == "tidas" else ops.tidas_adjoint
         fn = lambda: f(k, x, variant=a.variant)
     for _ in range(a.iters):
         fn()

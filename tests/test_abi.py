@@ -89,3 +89,13 @@ def test_null_arguments_are_rejected_before_any_launch():
     with pytest.raises(capi.TidasError) as e:  # GEMM needs 16-byte alignment
         capi.tidas_forward(16, 63, 8, 8, 18, 16, 1, capi.VARIANT_GEMM_BF16)
     assert e.value.code == capi.TIDAS_ERR_ARG
+
+
+def test_band_workspace_size():
+    # (rows x frame tiles x (2 per column tile + 2) chunks) x 16 KB for the
+    # GEMM variant of the 2D band calls; none for the direct variant
+    assert capi.tidas_band_workspace_bytes(1024, 512, 256, capi.VARIANT_GEMM_BF16) == \
+        1024 * 2 * 10 * 16384
+    assert capi.tidas_band_workspace_bytes(3, 24, 1, capi.VARIANT_GEMM_BF16) == 3 * 1 * 4 * 16384
+    assert capi.tidas_band_workspace_bytes(1024, 512, 256, capi.VARIANT_DIRECT) == 0
+    assert capi.tidas_band_workspace_bytes(0, 512, 256, capi.VARIANT_GEMM_BF16) == 0

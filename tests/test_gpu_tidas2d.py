@@ -192,3 +192,22 @@ def test_band_kernels_are_closer_to_exact_das_than_row_kernels():
     e1 = (o.tidas_forward(k1, refl).double() - das).norm() / das.norm()
     e2 = (o.tidas_forward_2d(P.fit_kernels_2d(31, 31), refl).double() - das).norm() / das.norm()
     assert float(e2) < float(e1), (float(e1), float(e2))
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_tidas2d_gemm_with_caller_workspace(adjoint):
+    # the caller-owned scratch gives the same values as the stream-ordered one;
+    # a scratch that is too small is refused before any launch
+    from paper_2507_15464_gb300 import capi
+    o = ops()
+    nf, nz, nx, kz, taps = 130, 21, 264, 7, 45
+    x, kern = _inputs(nf, nz, nx, kz, taps, 45)
+    xd, kd = to_dev(x).to(torch.bfloat16), to_dev(kern)
+    fn = o.tidas_adjoint_2d if adjoint else o.tidas_forward_2d
+    ref = fn(kd, xd, variant=1)
+    ws = o.band_workspace(nz, nx, nf, 1)
+    assert ws.numel() == nz * 2 * (2 * 3 + 2) * 16384
+    got = fn(kd, xd, variant=1, workspace=ws)
+    assert torch.equal(got, ref)
+    with pytest.raises(capi.TidasError):
+        fn(kd, xd, variant=1, workspace=ws[:-16])
