@@ -483,7 +483,8 @@ namespace gemm2 {
 constexpr int kStages = 3;
 constexpr int kStageBytes = 2 * gemm::kChunkBytes;  // two 64-column chunks
 constexpr int kBuilders = 6;  // warps 6 .. 11
-constexpr int kThreads = 32 * (6 + kBuilders);
+constexpr int kMma2Warp = 6 + kBuilders;           // second MMA issuer (tile 1)
+constexpr int kThreads = 32 * (kMma2Warp + 1);
 // The three Toeplitz tiles of a step (part cp = 0, 1, 2 of a tile's three
 // input chunks) are windows of one band matrix G[r][k], r in [-128, 128):
 // tile cp, row n = G row n - 64 cp.  G is 256 rows of 128 bytes (SW128).
@@ -578,14 +579,15 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
     const int it_begin = blockIdx.x, it_step = gridDim.x;
 
     if (threadIdx.x == 0) {
+        // the two MMA issuers both release stages, bands and accumulators
         for (int s = 0; s < gemm2::kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], 2);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&b_full[s], gemm2::kBuilders);
-            mbar_init(&b_empty[s], 1);
-            mbar_init(&acc_full[s], 1);
+            mbar_init(&b_empty[s], 2);
+            mbar_init(&acc_full[s], 2);
             mbar_init(&acc_empty[s], 4);
         }
         *s_abort = 0;
@@ -640,9 +642,15 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
             }
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // --------------------------------------------------- MMA issuer
+    } else if (warp == 1 || warp == gemm2::kMma2Warp) {
+        // ------------------------------------------------- MMA issuers
+        // Warp 1 issues the MMAs of the item's first column tile, the other
+        // issuer those of the second.  The tensor pipe queues about one MMA,
+        // so while one issuer waits on a barrier or commits, the other keeps
+        // the pipe fed.  Both wait for every stage and band and release
+        // every one, so a stage is refilled only after both are done with it.
         if (lane == 0) {
+            const int mine = warp == 1 ? 0 : 1;
             uint32_t st = 0, ph = 0;
             int step = 0, k = 0;
             bool stop = false;
@@ -685,11 +693,16 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
                                 mma_f16(d, a + 2 * kk, bb + 2 * kk, kIdesc,
                                         (kk > 0 || cp > 0) ? 1u : acc_u);
                         };
-                        const int t0 = c2 / 2 - I.s0;  // the pair is chunks 2 (s0 + t0), + 1
-                        if (t0 > 0) tile(t0 - 1, 2, 0);
-                        if (t0 < I.s1 - I.s0) {
-                            tile(t0, 0, 0);
-                            tile(t0, 1, 1);
+                        // the pair is chunks 2 (s0 + t0), + 1; tile `mine` takes
+                        // windows 0 and 1 of pair t0 = mine and window 2 of the next
+                        const int t0 = c2 / 2 - I.s0;
+                        if (mine < I.s1 - I.s0) {
+                            if (t0 == mine) {
+                                tile(mine, 0, 0);
+                                tile(mine, 1, 1);
+                            } else if (t0 == mine + 1) {
+                                tile(mine, 2, 0);
+                            }
                         }
                         mma_commit(&empty[st]);
                         if (++st == (uint32_t)gemm2::kStages) { st = 0; ph ^= 1; }
