@@ -370,3 +370,155 @@ void orc_tidas_conv2d_adjoint(int nz, int nx, int kz, int taps, int cz, int cx,
             r[(size_t)j * nx + xs] = acc;
         }
 }
+
+/* =========================================================================
+ * Single-line experiment of Section 3 (focused transmit, one image line on
+ * the array axis), in the channel domain of Eq. (2.8) -- Eq. (2.13).
+ *
+ * Geometry: the linear array above; the line is x = 0 with n_depths points
+ * z_i = z_first + (z_last - z_first) i / (n_depths - 1) (Section 3.1: 600
+ * points from 2 to 42 mm).  Scatterers sit on these points.
+ *
+ * Transmit (Section 3.1): focused on the axis at z_focus by the elements
+ * with |x_m| <= a_tx, where Kossoff's criterion with parameter kappa fixes
+ * the normalised focal distance z_focus / (a_tx^2 / lambda) = kappa, i.e.
+ * a_tx = sqrt(z_focus lambda / kappa), lambda = c / f0.  Element m fires at
+ * (z_focus - sqrt(x_m^2 + z_focus^2)) / c, so every wavelet reaches the
+ * focus at z_focus / c.  Receive: the elements with |x_n| <= z / (2 F#) of
+ * the depth z being focused (rectangular aperture, F# = fnum_rx).
+ *
+ * Channel data of a unit scatterer at (0, z_r), Eq. (2.1) / (2.6):
+ *   S_n(t_k) = sum_{m active} p(t_k - fire_m - |r - x_m| / c - |r - x_n| / c),
+ * t_k = k / fs, p the real pulse (envelope times cos), no spreading (R3).
+ * ========================================================================= */
+typedef struct {
+    int32_t n_elem;
+    double pitch, f0, fs, c, frac_bw;
+    int32_t n_samples;
+    int32_t n_depths;
+    double z_first, z_last;
+    double z_focus, kossoff, fnum_rx;
+    int32_t interp; /* 0 linear, 1 cubic (Keys, a = -0.5) */
+} orc_line;
+
+static double line_alpha(const orc_line* L) {
+    double half_bw = 0.5 * L->frac_bw * L->f0;
+    return M_PI * M_PI * half_bw * half_bw / log(pow(10.0, 6.0 / 20.0));
+}
+static double line_thalf(const orc_line* L) {
+    return sqrt(log(pow(10.0, 60.0 / 20.0)) / line_alpha(L));
+}
+double orc_line_elem_x(const orc_line* L, int n) {
+    return ((double)n - 0.5 * (double)(L->n_elem - 1)) * L->pitch;
+}
+double orc_line_depth(const orc_line* L, int i) {
+    return L->z_first + (L->z_last - L->z_first) * (double)i / (double)(L->n_depths - 1);
+}
+double orc_line_tx_radius(const orc_line* L) {
+    return sqrt(L->z_focus * (L->c / L->f0) / L->kossoff);
+}
+int orc_line_tx_active(const orc_line* L, int m) {
+    return fabs(orc_line_elem_x(L, m)) <= orc_line_tx_radius(L);
+}
+double orc_line_fire(const orc_line* L, int m) {
+    double xm = orc_line_elem_x(L, m);
+    return (L->z_focus - sqrt(xm * xm + L->z_focus * L->z_focus)) / L->c;
+}
+int orc_line_rx_active(const orc_line* L, int n, double z) {
+    return fabs(orc_line_elem_x(L, n)) <= z / (2.0 * L->fnum_rx);
+}
+/* Eq. (2.3): receive delay of element n for the on-axis point at depth z */
+double orc_line_delay(const orc_line* L, int n, double z) {
+    double xn = orc_line_elem_x(L, n);
+    return (z - sqrt(xn * xn + z * z)) / L->c;
+}
+/* echo arrival of the on-axis point at depth z on element n, with the
+ * transmit arrival z / c of the focused beam on its axis */
+double orc_line_arrival(const orc_line* L, int n, double z) {
+    double xn = orc_line_elem_x(L, n);
+    return z / L->c + sqrt(xn * xn + z * z) / L->c;
+}
+
+/* S[n][k] of a unit scatterer on line point r; S is overwritten */
+void orc_line_synth(const orc_line* L, int r, double* S) {
+    double alpha = line_alpha(L), thalf = line_thalf(L);
+    double zr = orc_line_depth(L, r);
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < L->n_elem; ++n) {
+        double xn = orc_line_elem_x(L, n);
+        double rx = sqrt(xn * xn + zr * zr) / L->c;
+        double* out = S + (size_t)n * L->n_samples;
+        for (int k = 0; k < L->n_samples; ++k) out[k] = 0.0;
+        for (int m = 0; m < L->n_elem; ++m) {
+            if (!orc_line_tx_active(L, m)) continue;
+            double xm = orc_line_elem_x(L, m);
+            double tau = orc_line_fire(L, m) + sqrt(xm * xm + zr * zr) / L->c + rx;
+            for (int k = 0; k < L->n_samples; ++k) {
+                double t = (double)k / L->fs - tau;
+                if (fabs(t) > thalf) continue;
+                out[k] += exp(-alpha * t * t) * cos(2.0 * M_PI * L->f0 * t);
+            }
+        }
+    }
+}
+
+static double line_interp(const orc_line* L, const double* row, double u) {
+    long fl = (long)floor(u);
+    double phi = u - (double)fl, acc = 0.0;
+    if (L->interp == 0) {
+        if (fl >= 0 && fl < L->n_samples) acc += (1.0 - phi) * row[fl];
+        if (fl + 1 >= 0 && fl + 1 < L->n_samples) acc += phi * row[fl + 1];
+        return acc;
+    }
+    for (long m = fl - 1; m <= fl + 2; ++m)
+        if (m >= 0 && m < L->n_samples) acc += orc_keys(u - (double)m) * row[m];
+    return acc;
+}
+
+/* DAS line (Eq. (2.2) with dynamic receive focusing): for every line point
+ * z_i, sum over the receive aperture of z_i of S_n at the echo arrival
+ * time of z_i, i.e. the aligned time 2 z_i / c minus D_n(z_i) of Eq. (2.3) */
+void orc_line_das(const orc_line* L, const double* S, double* g) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < L->n_depths; ++i) {
+        double zi = orc_line_depth(L, i), acc = 0.0;
+        for (int n = 0; n < L->n_elem; ++n) {
+            if (!orc_line_rx_active(L, n, zi)) continue;
+            double u = (2.0 * zi / L->c - orc_line_delay(L, n, zi)) * L->fs;
+            acc += line_interp(L, S + (size_t)n * L->n_samples, u);
+        }
+        g[i] = acc;
+    }
+}
+
+/* Window of Eq. (2.8): the samples of channel n whose time lies within eps
+ * of the echo arrival of line point r on that channel (chi^r = 1_B) */
+int orc_line_in_window(const orc_line* L, int r, double eps, int n, long k) {
+    double t = (double)k / L->fs - orc_line_arrival(L, n, orc_line_depth(L, r));
+    return fabs(t) <= eps;
+}
+
+/* Fixed-curve line of Eq. (2.8) / (2.13) without theta:
+ *   a[i] = sum_{n in aperture(z_s)} S~_n(2 z_i / c - D_n(z_s)),
+ * S~_n = S_n times the window of scatterer r (eps < 0: no window).  The
+ * delay set and the aperture are those of line point s for every z_i. */
+void orc_line_fixed(const orc_line* L, const double* S, int r, int s, double eps, double* a) {
+    double zs = orc_line_depth(L, s);
+    double* Sw = (double*)malloc(sizeof(double) * (size_t)L->n_elem * L->n_samples);
+    for (int n = 0; n < L->n_elem; ++n)
+        for (long k = 0; k < L->n_samples; ++k) {
+            size_t q = (size_t)n * L->n_samples + k;
+            Sw[q] = (eps < 0.0 || orc_line_in_window(L, r, eps, n, k)) ? S[q] : 0.0;
+        }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < L->n_depths; ++i) {
+        double zi = orc_line_depth(L, i), acc = 0.0;
+        for (int n = 0; n < L->n_elem; ++n) {
+            if (!orc_line_rx_active(L, n, zs)) continue;
+            double u = (2.0 * zi / L->c - orc_line_delay(L, n, zs)) * L->fs;
+            acc += line_interp(L, Sw + (size_t)n * L->n_samples, u);
+        }
+        a[i] = acc;
+    }
+    free(Sw);
+}
