@@ -211,6 +211,64 @@ int tidas_forward_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz,
 int tidas_adjoint_2d(const float* kernels, int32_t kz, int32_t taps, int32_t nz, int32_t nx,
                      const void* img, float* refl, int32_t n_frames, int32_t variant,
                      void* workspace, size_t workspace_bytes, void* stream);
+/* ------------------------------------------------------------------------
+ * Single-line experiment of Section 3 (Eq. (2.8), (2.12), (2.13) in the
+ * channel domain).  One image line on the array axis, x = 0, with n_depths
+ * points z_i = z_first + (z_last - z_first) i / (n_depths - 1); scatterers
+ * sit on these points.  Transmit: focused on the axis at z_focus by the
+ * elements with |x_m| <= a_tx, a_tx = sqrt(z_focus (c / f0) / kossoff)
+ * (Kossoff's criterion, normalised focal distance z_focus / (a_tx^2 /
+ * lambda) = kossoff); element m fires at (z_focus - |focus - x_m|) / c.
+ * Receive: the elements with |x_n| <= z / (2 fnum_rx) of the depth z being
+ * focused, unit weights.  Pulse: as in das_params (f0, frac_bw), real part.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_elem;            /* linear array, x_n = (n - (n_elem - 1) / 2) pitch */
+    double pitch, f0, fs, c, frac_bw;
+    int32_t n_samples;         /* channel record length, sample k at t = k / fs */
+    int32_t n_depths;          /* line points (>= 2) */
+    double z_first, z_last;    /* metres */
+    double z_focus;            /* transmit focus depth */
+    double kossoff;            /* Kossoff parameter of the transmit aperture (0.6) */
+    double fnum_rx;            /* receive F-number (1) */
+    int32_t interp;            /* TIDAS_INTERP_* */
+} tidas_line_params;
+
+/* Channel data rf[n_scat][n_elem][n_samples] (FP32, overwritten) of a unit
+ * scatterer on each line point r_first .. r_first + n_scat - 1 (Eq. (2.1),
+ * (2.6)): S_n(t_k) = sum_{m in transmit aperture} p(t_k - fire_m -
+ * |r - x_m| / c - |r - x_n| / c), summed over m in index order. */
+int tidas_line_synthesize(const tidas_line_params* p, int32_t r_first, int32_t n_scat,
+                          float* rf, void* stream);
+/* DAS lines lines[n_scat][n_depths] of the channel data rf[n_scat][n_elem]
+ * [n_samples] (Eq. (2.2) with dynamic receive focusing): point z_i sums,
+ * over the receive aperture of z_i, S_n at sample (2 z_i / c - D_n(z_i)) fs,
+ * D_n of Eq. (2.3), interpolated.  Uses a stream-ordered table of a few MB. */
+int tidas_line_das(const tidas_line_params* p, const float* rf, int32_t n_scat, float* lines,
+                   void* stream);
+/* Sweep of Eq. (2.8) / (2.12) over every delay curve s = 0 .. n_depths - 1
+ * for the scatterers on points r_first .. r_first + n_scat - 1, given their
+ * channel data rf[n_scat][n_elem][n_samples] and DAS lines
+ * lines[n_scat][n_depths]:
+ *   a_s[i] = sum_{n in aperture(z_s)} S~_n((2 z_i / c - D_n(z_s)) fs),
+ * S~_n = the samples within eps seconds of the scatterer's echo arrival on
+ * channel n (z_r / c + |r - x_n| / c), zero elsewhere; b = a_r (its own
+ * curve).  Outputs, [n_depths][n_scat] (row = delay curve s, column =
+ * scatterer), FP32:
+ *   theta     = <a_s, b> / <a_s, a_s>                   (Eq. (2.12); 0 if a_s = 0)
+ *   err_local = sum_W (theta a_s - g)^2 / sum_W g^2,  W = {i : |z_i - z_r| <= c eps / 2}
+ *   err_global= sum_i (theta a_s - g)^2 / sum_i g^2,  g the DAS line.
+ * 2 eps fs + 1 must stay below 27 samples (TIDAS_ERR_UNSUPPORTED otherwise);
+ * n_elem x 136 + n_depths x 40 bytes of shared memory must fit in 220 KB. */
+int tidas_line_sweep(const tidas_line_params* p, const float* rf, const float* lines,
+                     int32_t r_first, int32_t n_scat, double eps, float* theta,
+                     float* err_local, float* err_global, void* stream);
+/* The window half-width of Section 3.2: half the FWHM of the DAS PSF at the
+ * focal point.  There the transmit and receive delays align every
+ * contribution, so the PSF's time profile is the pulse and
+ * *eps = sqrt(ln 2 / alpha), alpha the envelope rate of the pulse. */
+int tidas_line_window(const tidas_line_params* p, double* eps);
+
 /* Scratch bytes of the 2D band calls: the input repacked into the GEMM's
  * operand tiles (128 frames x 64 columns, 16 KB each, per row); 0 for
  * variants that need none or for invalid sizes. */

@@ -34,6 +34,18 @@ class das_params(ctypes.Structure):
     ]
 
 
+class line_params(ctypes.Structure):
+    """Mirror of tidas_line_params (include/tidas.h), field for field."""
+    _fields_ = [
+        ("n_elem", ctypes.c_int32), ("pitch", ctypes.c_double), ("f0", ctypes.c_double),
+        ("fs", ctypes.c_double), ("c", ctypes.c_double), ("frac_bw", ctypes.c_double),
+        ("n_samples", ctypes.c_int32), ("n_depths", ctypes.c_int32),
+        ("z_first", ctypes.c_double), ("z_last", ctypes.c_double),
+        ("z_focus", ctypes.c_double), ("kossoff", ctypes.c_double),
+        ("fnum_rx", ctypes.c_double), ("interp", ctypes.c_int32),
+    ]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
 _S = ctypes.c_size_t
@@ -76,6 +88,11 @@ _SIG = {
     "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
     "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],
     "tidas_band_workspace_bytes": [_I, _I, _I, _I],
+    "tidas_line_synthesize": [ctypes.POINTER(line_params), _I, _I, _P, _P],
+    "tidas_line_das": [ctypes.POINTER(line_params), _P, _I, _P, _P],
+    "tidas_line_sweep": [ctypes.POINTER(line_params), _P, _P, _I, _I, ctypes.c_double, _P, _P,
+                         _P, _P],
+    "tidas_line_window": [ctypes.POINTER(line_params), ctypes.POINTER(ctypes.c_double)],
 }
 _RESTYPE = {"tidas_band_workspace_bytes": _S}
 EXPORTED = list(_SIG) + ["tidas_last_error"]
@@ -175,6 +192,25 @@ def tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant, wo
                      workspace_bytes=0, stream=0):
     return _check(load().tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant,
                                           workspace, workspace_bytes, stream))
+
+
+def tidas_line_synthesize(p, r_first, n_scat, rf, stream=0):
+    return _check(load().tidas_line_synthesize(ctypes.byref(p), r_first, n_scat, rf, stream))
+
+
+def tidas_line_das(p, rf, n_scat, lines, stream=0):
+    return _check(load().tidas_line_das(ctypes.byref(p), rf, n_scat, lines, stream))
+
+
+def tidas_line_sweep(p, rf, lines, r_first, n_scat, eps, theta, err_local, err_global, stream=0):
+    return _check(load().tidas_line_sweep(ctypes.byref(p), rf, lines, r_first, n_scat, eps, theta,
+                                          err_local, err_global, stream))
+
+
+def tidas_line_window(p):
+    eps = ctypes.c_double()
+    _check(load().tidas_line_window(ctypes.byref(p), ctypes.byref(eps)))
+    return eps.value
 
 
 def tidas_band_workspace_bytes(nz, nx, n_frames, variant):

@@ -12,6 +12,15 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
                         const void* in, float* out, int nf, void* workspace, size_t ws_bytes,
                         cudaStream_t st);
 size_t band_pack_bytes(int nz, int nx, int nf);
+int validate_line(const tidas_line_params* p);
+double line_window(const tidas_line_params& p);
+int launch_line_synth(const tidas_line_params& p, int r_first, int n_scat, float* rf,
+                      cudaStream_t st);
+int launch_line_das(const tidas_line_params& p, const float* rf, int n_scat, float* lines,
+                    cudaStream_t st);
+int launch_line_sweep(const tidas_line_params& p, const float* rf, const float* lines,
+                      int r_first, int n_scat, double eps, float* theta, float* e_loc,
+                      float* e_glob, cudaStream_t st);
 int launch_fit_kernels_2d(const Plan& P, int kz, int taps, float* kernels, cudaStream_t st);
 }  // namespace tidas
 
@@ -177,4 +186,45 @@ extern "C" int tidas_adjoint_2d(const float* kernels, int32_t kz, int32_t taps, 
                                 void* stream) {
     return tidas2d_common("tidas_adjoint_2d", kernels, kz, taps, nz, nx, img, refl, n_frames,
                           variant, workspace, workspace_bytes, true, stream);
+}
+
+// ------------------------------------------------ single-line experiment
+extern "C" int tidas_line_synthesize(const tidas_line_params* p, int32_t r_first, int32_t n_scat,
+                                     float* rf, void* stream) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(rf, "tidas_line_synthesize: null rf");
+    TIDAS_REQUIRE(n_scat >= 1 && n_scat <= 65535 && r_first >= 0 && r_first + n_scat <= p->n_depths,
+                  "tidas_line_synthesize: scatterers outside the line");
+    return launch_line_synth(*p, r_first, n_scat, rf, S_(stream));
+}
+
+extern "C" int tidas_line_das(const tidas_line_params* p, const float* rf, int32_t n_scat,
+                              float* lines, void* stream) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(rf && lines, "tidas_line_das: null pointer");
+    TIDAS_REQUIRE(n_scat >= 1 && n_scat <= 65535, "tidas_line_das: bad n_scat");
+    return launch_line_das(*p, rf, n_scat, lines, S_(stream));
+}
+
+extern "C" int tidas_line_sweep(const tidas_line_params* p, const float* rf, const float* lines,
+                                int32_t r_first, int32_t n_scat, double eps, float* theta,
+                                float* err_local, float* err_global, void* stream) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(rf && lines && theta && err_local && err_global, "tidas_line_sweep: null pointer");
+    TIDAS_REQUIRE(n_scat >= 1 && r_first >= 0 && r_first + n_scat <= p->n_depths,
+                  "tidas_line_sweep: scatterers outside the line");
+    TIDAS_REQUIRE(eps > 0.0, "tidas_line_sweep: eps must be positive");
+    return launch_line_sweep(*p, rf, lines, r_first, n_scat, eps, theta, err_local, err_global,
+                             S_(stream));
+}
+
+extern "C" int tidas_line_window(const tidas_line_params* p, double* eps) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(eps, "tidas_line_window: null eps");
+    *eps = line_window(*p);
+    return TIDAS_OK;
 }

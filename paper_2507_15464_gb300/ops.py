@@ -190,3 +190,48 @@ def tidas_forward_2d(kernels, refl, variant=capi.VARIANT_DIRECT, out=None, works
 
 def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None, workspace=None):
     return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out, workspace)
+
+
+class LineExperiment:
+    """The single-line experiment of Section 3 on the GPU: channel data of a
+    unit scatterer on every line point, DAS lines, and the sweep of Eq. (2.8)
+    / (2.12) over every (delay curve, scatterer) pair.  `p` is a dict with the
+    tidas_line_params fields."""
+
+    def __init__(self, p: dict):
+        self.p = dict(p)
+        self.P = capi.line_params(**{k: self.p[k] for k, _ in capi.line_params._fields_})
+        self.N, self.S, self.D = self.P.n_elem, self.P.n_samples, self.P.n_depths
+
+    def window(self):
+        """Half the FWHM of the focal-point PSF (the window of Section 3.2)."""
+        return capi.tidas_line_window(self.P)
+
+    def depth(self, i):
+        return self.P.z_first + (self.P.z_last - self.P.z_first) * i / (self.D - 1)
+
+    def synthesize(self, r_first=0, n_scat=None, out=None, device="cuda"):
+        n_scat = self.D - r_first if n_scat is None else n_scat
+        out = out if out is not None else torch.empty((n_scat, self.N, self.S),
+                                                      dtype=torch.float32, device=device)
+        _need(out, torch.float32, (n_scat, self.N, self.S), "rf")
+        capi.tidas_line_synthesize(self.P, r_first, n_scat, _ptr(out), _stream())
+        return out
+
+    def das_lines(self, rf, out=None):
+        n = rf.shape[0]
+        _need(rf, torch.float32, (n, self.N, self.S), "rf")
+        out = out if out is not None else torch.empty((n, self.D), dtype=torch.float32,
+                                                      device=rf.device)
+        capi.tidas_line_das(self.P, _ptr(rf), n, _ptr(out), _stream())
+        return out
+
+    def sweep(self, rf, lines, eps, r_first=0):
+        """theta, local error, global error: [n_depths curves, n_scat scatterers]."""
+        n = rf.shape[0]
+        _need(rf, torch.float32, (n, self.N, self.S), "rf")
+        _need(lines, torch.float32, (n, self.D), "lines")
+        outs = [torch.empty((self.D, n), dtype=torch.float32, device=rf.device) for _ in range(3)]
+        capi.tidas_line_sweep(self.P, _ptr(rf), _ptr(lines), r_first, n, float(eps),
+                              *[_ptr(o) for o in outs], _stream())
+        return tuple(outs)

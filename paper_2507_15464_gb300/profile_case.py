@@ -3,6 +3,7 @@
 python -m paper_2507_15464_gb300.profile_case das --frames 8 --dtype f16 --iters 3
 python -m paper_2507_15464_gb300.profile_case tidas --variant 1 --frames 64 --iters 3
 python -m paper_2507_15464_gb300.profile_case tidas2d --variant 1 --kz 16 --frames 256 --iters 3
+python -m paper_2507_15464_gb300.profile_case line --iters 2
 
 Inputs are seeded random arrays of the benchmark's shapes (the kernels'
 cost does not depend on the values); nothing is checked here.
@@ -18,7 +19,7 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["das", "das_adjoint", "tidas", "tidas_adjoint", "tidas2d",
-                                        "tidas2d_adjoint"])
+                                        "tidas2d_adjoint", "line"])
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--dtype", default="f16", choices=["f16", "f32"])
     ap.add_argument("--variant", type=int, default=0)
@@ -32,7 +33,21 @@ def main():
     from tidas_workloads import presets
     g = presets.geometry(a.geom)
     gen = torch.Generator(device="cuda").manual_seed(0)
-    if a.case in ("das", "das_adjoint"):
+    if a.case == "line":
+        # the single-line experiment: 600 points, 192 elements, focus 25 mm
+        p = dict(n_elem=192, pitch=0.3e-3, f0=5e6, fs=40e6, c=1540.0, frac_bw=0.6,
+                 n_samples=2560, n_depths=600, z_first=2e-3, z_last=42e-3, z_focus=25e-3,
+                 kossoff=0.6, fnum_rx=1.0, interp=1)
+        E = ops.LineExperiment(p)
+        eps = E.window()
+        rf = E.synthesize()
+        lines = E.das_lines(rf)
+
+        def fn():
+            E.synthesize(out=rf)
+            E.das_lines(rf, out=lines)
+            E.sweep(rf, lines, eps)
+    elif a.case in ("das", "das_adjoint"):
         dt = torch.float16 if (a.dtype == "f16" and a.case == "das") else torch.float32
         P = ops.DasPlan(g, rf_dtype=dt)
         if a.case == "das":

@@ -47,6 +47,34 @@ def test_params_struct_layout_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     flat = re.findall(r"(\w+)\s*[,;]", body)
     assert flat == [f[0] for f in capi.das_params._fields_]
+    start = text.index("} das_params;")
+    body = text[text.index("typedef struct {", start) + len("typedef struct {"):
+                text.index("} tidas_line_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    assert re.findall(r"(\w+)\s*[,;]", body) == [f[0] for f in capi.line_params._fields_]
+
+
+def _line(**kw):
+    vals = dict(n_elem=64, pitch=3e-4, f0=5e6, fs=4e7, c=1540.0, frac_bw=0.6, n_samples=1024,
+                n_depths=41, z_first=5e-3, z_last=25e-3, z_focus=15e-3, kossoff=0.6,
+                fnum_rx=1.0, interp=1)
+    vals.update(kw)
+    return capi.line_params(**vals)
+
+
+@pytest.mark.parametrize("bad", [dict(n_elem=0), dict(n_depths=1), dict(z_first=0.0),
+                                 dict(z_last=4e-3), dict(kossoff=0.0), dict(interp=2),
+                                 dict(n_elem=2000)])
+def test_line_calls_reject_bad_parameters(bad):
+    # refused on the host by the parameter check itself (null outputs would be
+    # refused after it, so the message tells which check fired)
+    with pytest.raises(capi.TidasError) as e:
+        capi.tidas_line_synthesize(_line(**bad), 0, 1, None)
+    assert "null" not in str(e.value)
+    with pytest.raises(capi.TidasError) as e:
+        capi.tidas_line_das(_line(**bad), None, 1, None)
+    assert "null" not in str(e.value)
+
 
 
 def _params(**kw):
@@ -99,3 +127,13 @@ def test_band_workspace_size():
     assert capi.tidas_band_workspace_bytes(3, 24, 1, capi.VARIANT_GEMM_BF16) == 3 * 1 * 4 * 16384
     assert capi.tidas_band_workspace_bytes(1024, 512, 256, capi.VARIANT_DIRECT) == 0
     assert capi.tidas_band_workspace_bytes(0, 512, 256, capi.VARIANT_GEMM_BF16) == 0
+
+
+def test_line_window_is_half_the_envelope_fwhm():
+    # host-side closed form, checked against the oracle's (itself pinned to a
+    # numerical FWHM of the envelope)
+    from oracle.line import LineOracle, paper_line
+    for f0 in (5e6, 7e6):
+        p = paper_line(f0=f0)
+        eps = capi.tidas_line_window(capi.line_params(**p))
+        assert eps == pytest.approx(LineOracle(p).eps(), rel=1e-15)
