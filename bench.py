@@ -457,10 +457,10 @@ def bench_line(torch, stream):
     import time
 
     from paper_2507_15464_gb300.ops import LineExperiment
-    import oracle.line as oline
+    from tidas_workloads.line_scenarios import paper_line
     res = {}
     for f0, zf in ((5e6, 25e-3), (7e6, 25e-3), (5e6, 15e-3), (5e6, 35e-3)):
-        p = oline.paper_line(f0=f0, z_focus=zf)
+        p = paper_line(f0=f0, z_focus=zf)
         E = LineExperiment(p)
         eps = E.window()
         rf = E.synthesize()
@@ -492,6 +492,7 @@ def bench_line(torch, stream):
         if f0 == 5e6 and zf == 25e-3:
             # sampled pairs against the FP64 oracle on the same channel data,
             # and the oracle's own rate on a bounded sample (about 10 s)
+            import oracle.line as oline
             O = oline.LineOracle(p)
             rf_h, g_h = rf.cpu().numpy(), g.cpu().numpy()
             errs = []
@@ -510,8 +511,62 @@ def bench_line(torch, stream):
             r["oracle_pairs_per_s"] = n_or / dt
             r["paper_table_3_2"] = {"das_min": 28.35, "tidas_min": 21.11,
                                     "note": "Python on unstated hardware; context only"}
+            r["line_reconstruction"] = bench_line_reconstruction(torch, stream, E, rf, th, eps)
         res[key] = r
         del rf, g
+    return res
+
+
+def bench_line_reconstruction(torch, stream, E, rf, theta, eps):
+    """Section 3.4 / Table 3.1: lines of 5 and 100 scatterers reconstructed by
+    DAS and by the line model of Eq. (2.13) with the delay curves of the 25
+    and 35 mm points (theta: that curve's row of the sweep); envelopes on the
+    GPU, mean side-lobe levels outside the main lobes (-20 dB pulse width)."""
+    from paper_2507_15464_gb300.ops import envelope
+    from tidas_workloads.line_scenarios import scenarios
+    D = E.D
+    z = np.array([E.depth(i) for i in range(D)])
+    # main-lobe half-width in depth: the pulse envelope 20 dB down, two-way
+    alpha = np.log(2.0) / eps ** 2
+    half = E.p["c"] * np.sqrt(np.log(10.0) / alpha) / 2.0
+
+    def sl_db(env, pts):
+        side = np.ones(D, bool)
+        for j in pts:
+            side &= np.abs(z - z[j]) > half
+        return float(20.0 * np.log10(env[side].mean() / env.max()))
+
+    def timed(fn, reps=20):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    for name, amps in scenarios(D).items():
+        pts = np.nonzero(amps)[0]
+        S = E.combine(rf, torch.from_numpy(amps.astype(np.float32)).cuda())
+        S1 = S.reshape(1, *S.shape)
+        das = E.das_lines(S1)[0]
+        env_das = envelope(das).cpu().numpy()
+        out = {"scatterers": int(pts.size), "das_line_ms": timed(lambda: E.das_lines(S1))}
+        for zs in (25e-3, 35e-3):
+            s = int(np.argmin(np.abs(z - zs)))
+            th = theta[s].contiguous()
+            ti = E.model(S, s, th, eps)
+            env_ti = envelope(ti).cpu().numpy()
+            sd, st_ = sl_db(env_das, pts), sl_db(env_ti, pts)
+            out["curve_%gmm" % (zs * 1e3)] = {
+                "tidas_line_ms": timed(lambda: E.model(S, s, th, eps)),
+                "mean_sl_das_db": sd, "mean_sl_tidas_db": st_,
+                "relative_sl_error": abs(st_ - sd) / abs(sd),
+                "peak_ratio_tidas_over_das": float(env_ti[pts].mean() / env_das[pts].mean())}
+        res[name] = out
+    res["paper_table_3_1"] = "parity unpinned: the paper's SL definition and line geometry are not given"
     return res
 
 

@@ -268,6 +268,23 @@ int tidas_line_sweep(const tidas_line_params* p, const float* rf, const float* l
  * contribution, so the PSF's time profile is the pulse and
  * *eps = sqrt(ln 2 / alpha), alpha the envelope rate of the pulse. */
 int tidas_line_window(const tidas_line_params* p, double* eps);
+/* Channel data of a line of scatterers from unit-scatterer data (Eq. (2.1)
+ * is linear in the reflectivity): rf_line[n][k] = sum_r amps[r]
+ * rf[r][n][k] over rf[n_scat][n_elem][n_samples], amps[n_scat] (device);
+ * summed in the order of r, zero amplitudes skipped.  n_scat <= 8192. */
+int tidas_line_combine(const tidas_line_params* p, const float* rf, int32_t n_scat,
+                       const float* amps, float* rf_line, void* stream);
+/* Line model of Eq. (2.13) on line channel data rf_line[n_elem][n_samples]:
+ *   out[i] = theta[i] * sum_{n in aperture(z_s)} S~^(i)_n((2 z_i / c - D_n(z_s)) fs),
+ * S~^(i)_n the samples within eps of the echo arrival of point i on channel
+ * n (the window of Eq. (2.8) for a scatterer on point i); theta[n_depths]
+ * (device), typically row s of tidas_line_sweep's theta. */
+int tidas_line_model(const tidas_line_params* p, const float* rf_line, int32_t s,
+                     const float* theta, double eps, float* out, void* stream);
+/* Envelope (modulus of the analytic signal) of n_rows real rows of length n
+ * (x, env: [n_rows][n], device): the DFT with negative frequencies removed
+ * and positive ones doubled, inverted.  n <= 18000. */
+int tidas_line_envelope(int32_t n_rows, int32_t n, const float* x, float* env, void* stream);
 
 /* Scratch bytes of the 2D band calls: the input repacked into the GEMM's
  * operand tiles (128 frames x 64 columns, 16 KB each, per row); 0 for

@@ -58,6 +58,7 @@ _SIG = {
     "orc_line_in_window": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_long]),
     "orc_line_fixed": (None, [_P, _D, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]),
+    "orc_line_model": (None, [_P, _D, ctypes.c_int, _D, ctypes.c_double, _D]),
 }
 _lib = None
 
@@ -149,6 +150,28 @@ class LineOracle:
         self.L.orc_line_fixed(self._p(), _dp(S), int(r), int(s), float(eps), _dp(a))
         return a
 
+    def line_data(self, amps):
+        """Channel data of a line of scatterers: amps[r] on point r (Eq. (2.1)
+        is linear in the reflectivity)."""
+        S = np.zeros((self.N, self.S))
+        for r in np.nonzero(amps)[0]:
+            S += amps[r] * self.synth(r)
+        return S
+
+    def model_line(self, S, s, theta, eps):
+        """Eq. (2.13): the line model with delay curve s and weights theta[i]."""
+        S = _f64(S)
+        th = _f64(theta)
+        assert th.size == self.D
+        out = np.empty(self.D)
+        self.L.orc_line_model(self._p(), _dp(S), int(s), _dp(th), float(eps), _dp(out))
+        return out
+
+    def mainlobe_halfwidth(self):
+        """Half-width in depth of a scatterer's main lobe: where the pulse
+        envelope is 20 dB down, t = sqrt(ln 10 / alpha), two-way: c t / 2."""
+        return self.P.c * np.sqrt(np.log(10.0) / self.alpha()) / 2.0
+
     # -- Eq. (2.12) and the errors of Section 3.3 -----------------------------
     def local_points(self, r, eps):
         z = self.depths()
@@ -169,10 +192,34 @@ class LineOracle:
         return theta, e_loc, e_glob
 
 
-def paper_line(f0=5e6, z_focus=25e-3, n_depths=600, n_elem=192, n_samples=2560):
-    """The line experiment of Section 3.1: 600 points from 2 to 42 mm, focus
-    on the axis, Kossoff 0.6 transmit aperture, F# 1 receive aperture; a
-    192-element, 0.3 mm pitch array sampled at 40 MHz (Section 2.1)."""
-    return dict(n_elem=n_elem, pitch=0.3e-3, f0=f0, fs=40e6, c=1540.0, frac_bw=0.6,
-                n_samples=n_samples, n_depths=n_depths, z_first=2e-3, z_last=42e-3,
-                z_focus=z_focus, kossoff=0.6, fnum_rx=1.0, interp=1)
+# the experiment's parameters and scenes are inputs, shared with the GPU side
+from tidas_workloads.line_scenarios import paper_line, scenarios as line_scenarios  # noqa: E402,F401
+
+
+# -- line-reconstruction metrics (Section 3.4, Table 3.1) -----------------------
+def envelope(x):
+    """|analytic signal| of a real sequence: the spectrum's negative
+    frequencies removed, the positive ones doubled (discrete Hilbert
+    transform)."""
+    x = np.asarray(x, np.float64)
+    n = x.size
+    h = np.zeros(n)
+    h[0] = 1.0
+    if n % 2 == 0:
+        h[n // 2] = 1.0
+        h[1:n // 2] = 2.0
+    else:
+        h[1:(n + 1) // 2] = 2.0
+    return np.abs(np.fft.ifft(np.fft.fft(x) * h))
+
+
+def sidelobe_level_db(env, z, points, halfwidth):
+    """Mean side-lobe level (dB): the mean envelope over the line points
+    outside every scatterer's main lobe (|z - z_j| > halfwidth), relative to
+    the envelope's maximum."""
+    env = np.asarray(env, np.float64)
+    z = np.asarray(z, np.float64)
+    side = np.ones(z.size, bool)
+    for j in points:
+        side &= np.abs(z - z[j]) > halfwidth
+    return float(20.0 * np.log10(env[side].mean() / env.max()))

@@ -522,3 +522,37 @@ void orc_line_fixed(const orc_line* L, const double* S, int r, int s, double eps
     }
     free(Sw);
 }
+
+/* Line model of Eq. (2.13) on channel data S[n_elem][n_samples] of a whole
+ * line (any scatterers): for every line point i,
+ *   L_i = theta[i] * sum_{n in aperture(z_s)} S~^(i)_n((2 z_i / c - D_n(z_s)) fs),
+ * S~^(i)_n = the samples of channel n within eps of the echo arrival of point
+ * i (the window of Eq. (2.8) for a scatterer on point i).  Plain loops over
+ * the interpolation taps, each tested against the window. */
+void orc_line_model(const orc_line* L, const double* S, int s, const double* theta, double eps,
+                    double* out) {
+    double zs = orc_line_depth(L, s);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < L->n_depths; ++i) {
+        double zi = orc_line_depth(L, i), acc = 0.0;
+        for (int n = 0; n < L->n_elem; ++n) {
+            if (!orc_line_rx_active(L, n, zs)) continue;
+            double u = (2.0 * zi / L->c - orc_line_delay(L, n, zs)) * L->fs;
+            double t_i = orc_line_arrival(L, n, zi);
+            long fl = (long)floor(u);
+            double phi = u - (double)fl;
+            const double* row = S + (size_t)n * L->n_samples;
+            for (long m = fl - 1; m <= fl + 2; ++m) {
+                if (m < 0 || m >= L->n_samples) continue;
+                if (!(fabs((double)m / L->fs - t_i) <= eps)) continue;
+                double w;
+                if (L->interp == 0)
+                    w = (m == fl) ? 1.0 - phi : (m == fl + 1) ? phi : 0.0;
+                else
+                    w = orc_keys(u - (double)m);
+                acc += w * row[m];
+            }
+        }
+        out[i] = theta[i] * acc;
+    }
+}

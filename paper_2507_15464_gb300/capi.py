@@ -93,6 +93,9 @@ _SIG = {
     "tidas_line_sweep": [ctypes.POINTER(line_params), _P, _P, _I, _I, ctypes.c_double, _P, _P,
                          _P, _P],
     "tidas_line_window": [ctypes.POINTER(line_params), ctypes.POINTER(ctypes.c_double)],
+    "tidas_line_combine": [ctypes.POINTER(line_params), _P, _I, _P, _P, _P],
+    "tidas_line_model": [ctypes.POINTER(line_params), _P, _I, _P, ctypes.c_double, _P, _P],
+    "tidas_line_envelope": [_I, _I, _P, _P, _P],
 }
 _RESTYPE = {"tidas_band_workspace_bytes": _S}
 EXPORTED = list(_SIG) + ["tidas_last_error"]
@@ -211,6 +214,18 @@ def tidas_line_window(p):
     eps = ctypes.c_double()
     _check(load().tidas_line_window(ctypes.byref(p), ctypes.byref(eps)))
     return eps.value
+
+
+def tidas_line_combine(p, rf, n_scat, amps, rf_line, stream=0):
+    return _check(load().tidas_line_combine(ctypes.byref(p), rf, n_scat, amps, rf_line, stream))
+
+
+def tidas_line_model(p, rf_line, s, theta, eps, out, stream=0):
+    return _check(load().tidas_line_model(ctypes.byref(p), rf_line, s, theta, eps, out, stream))
+
+
+def tidas_line_envelope(n_rows, n, x, env, stream=0):
+    return _check(load().tidas_line_envelope(n_rows, n, x, env, stream))
 
 
 def tidas_band_workspace_bytes(nz, nx, n_frames, variant):

@@ -14,6 +14,11 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
 size_t band_pack_bytes(int nz, int nx, int nf);
 int validate_line(const tidas_line_params* p);
 double line_window(const tidas_line_params& p);
+int launch_line_combine(const tidas_line_params& p, const float* rf, int n_scat, const float* amps,
+                        float* out, cudaStream_t st);
+int launch_line_model(const tidas_line_params& p, const float* S, int s, const float* theta,
+                      double eps, float* out, cudaStream_t st);
+int launch_line_envelope(int n_rows, int n, const float* x, float* env, cudaStream_t st);
 int launch_line_synth(const tidas_line_params& p, int r_first, int n_scat, float* rf,
                       cudaStream_t st);
 int launch_line_das(const tidas_line_params& p, const float* rf, int n_scat, float* lines,
@@ -227,4 +232,31 @@ extern "C" int tidas_line_window(const tidas_line_params* p, double* eps) {
     TIDAS_REQUIRE(eps, "tidas_line_window: null eps");
     *eps = line_window(*p);
     return TIDAS_OK;
+}
+
+extern "C" int tidas_line_combine(const tidas_line_params* p, const float* rf, int32_t n_scat,
+                                  const float* amps, float* rf_line, void* stream) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(rf && amps && rf_line, "tidas_line_combine: null pointer");
+    TIDAS_REQUIRE(n_scat >= 1 && n_scat <= 8192, "tidas_line_combine: need 1 <= n_scat <= 8192");
+    return launch_line_combine(*p, rf, n_scat, amps, rf_line, S_(stream));
+}
+
+extern "C" int tidas_line_model(const tidas_line_params* p, const float* rf_line, int32_t s,
+                                const float* theta, double eps, float* out, void* stream) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(rf_line && theta && out, "tidas_line_model: null pointer");
+    TIDAS_REQUIRE(s >= 0 && s < p->n_depths, "tidas_line_model: curve outside the line");
+    TIDAS_REQUIRE(eps > 0.0, "tidas_line_model: eps must be positive");
+    return launch_line_model(*p, rf_line, s, theta, eps, out, S_(stream));
+}
+
+extern "C" int tidas_line_envelope(int32_t n_rows, int32_t n, const float* x, float* env,
+                                   void* stream) {
+    TIDAS_REQUIRE(x && env, "tidas_line_envelope: null pointer");
+    TIDAS_REQUIRE(n_rows >= 1 && n_rows <= 65535 && n >= 1 && n <= 18000,
+                  "tidas_line_envelope: need 1 <= n_rows <= 65535 and 1 <= n <= 18000");
+    return launch_line_envelope(n_rows, n, x, env, S_(stream));
 }

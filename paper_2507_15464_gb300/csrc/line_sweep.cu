@@ -14,6 +14,7 @@
 // (apertures, windows, sample indices) is made in FP64 with the operations
 // rounded one at a time, so that it matches a plain FP64 evaluation exactly;
 // the sums run in FP32.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -398,6 +399,100 @@ __global__ void __launch_bounds__(32 * line::kSweepWarps) line_sweep_kernel(
     }
 }
 
+// ------------------------------------------------------- line reconstruction
+// Channel data of a line of scatterers from the unit-scatterer data (Eq. (2.1)
+// is linear in the reflectivity): out[n][k] = sum_r amps[r] rf[r][n][k], in
+// the order of r; zero amplitudes are skipped.
+__global__ void __launch_bounds__(256) line_combine_kernel(int n_scat, size_t row_len,
+                                                           const float* __restrict__ rf,
+                                                           const float* __restrict__ amps,
+                                                           float* __restrict__ out) {
+    extern __shared__ int s_nz[];  // indices of the non-zero amplitudes, in order
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int r = 0; r < n_scat; ++r)
+            if (amps[r] != 0.f) s_nz[c++] = r;
+        s_cnt = c;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < row_len;
+         q += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int j = 0; j < cnt; ++j) acc += amps[s_nz[j]] * __ldg(rf + (size_t)s_nz[j] * row_len + q);
+        out[q] = acc;
+    }
+}
+
+// Eq. (2.13): L_i = theta_i sum_{n in aperture(z_s)} S~^(i)_n at (2 z_i / c -
+// D_n(z_s)) fs, S~^(i) the samples within eps of point i's echo arrival.
+// Warp per line point, lanes over elements; positions and window decisions
+// in FP64, taps and sums in FP32.
+__global__ void __launch_bounds__(256) line_model_kernel(line::Dev L, const float* __restrict__ S,
+                                                         int s, const float* __restrict__ theta,
+                                                         double eps, float* __restrict__ out) {
+    using namespace line;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + warp;
+    if (i >= L.D) return;
+    const double zi = depth(L, i), zs = depth(L, s);
+    float acc = 0.f;
+    for (int n = lane; n < L.N; n += 32) {
+        const double xn = elem_x(L, n);
+        if (!rx_active(L, xn, zs)) continue;
+        const double u = __dmul_rn(__dsub_rn(__ddiv_rn(__dmul_rn(2.0, zi), L.c), delay(L, xn, zs)), L.fs);
+        const double t_i = arrival(L, xn, zi);
+        const double fl = floor(u);
+        const int idx = (int)fl;
+        const float* row = S + (size_t)n * L.S;
+        acc += interp(L.interp, idx, (float)(u - fl), [&](int k) {
+            if (k < 0 || k >= L.S) return 0.f;
+            return fabs(__dsub_rn(__ddiv_rn((double)k, L.fs), t_i)) <= eps ? __ldg(row + k) : 0.f;
+        });
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[i] = theta[i] * acc;
+}
+
+// |analytic signal| of each row x[j] (length n): the DFT, negative
+// frequencies removed and positive ones doubled, the inverse DFT, its
+// modulus.  O(n^2) per row, phases reduced exactly as (j k mod n) / n.
+__global__ void __launch_bounds__(256) line_envelope_kernel(int n, const float* __restrict__ x,
+                                                            float* __restrict__ env) {
+    extern __shared__ float sm[];
+    float* xs = sm;           // [n]
+    float2* X = (float2*)(sm + ((n + 1) & ~1));  // [n]
+    const float* xr = x + (size_t)blockIdx.x * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = xr[j];
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        float re = 0.f, im = 0.f;
+        for (int j = 0; j < n; ++j) {
+            const int q = (int)(((long long)j * k) % n);
+            float sn, cs;
+            sincospif(2.f * (float)q / (float)n, &sn, &cs);
+            re += xs[j] * cs;
+            im -= xs[j] * sn;
+        }
+        const float h = (k == 0 || 2 * k == n) ? 1.f : (2 * k < n ? 2.f : 0.f);
+        X[k] = make_float2(h * re, h * im);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float re = 0.f, im = 0.f;
+        for (int k = 0; k < n; ++k) {
+            const int q = (int)(((long long)j * k) % n);
+            float sn, cs;
+            sincospif(2.f * (float)q / (float)n, &sn, &cs);
+            re += X[k].x * cs - X[k].y * sn;
+            im += X[k].x * sn + X[k].y * cs;
+        }
+        env[(size_t)blockIdx.x * n + j] = sqrtf(re * re + im * im) / (float)n;
+    }
+}
+
 // ------------------------------------------------------------------ launch
 static line::Dev line_dev(const tidas_line_params& p) {
     line::Dev L;
@@ -518,4 +613,32 @@ int launch_line_sweep(const tidas_line_params& p, const float* rf, const float* 
     return rc;
 }
 
+}  // namespace tidas
+
+namespace tidas {
+int launch_line_combine(const tidas_line_params& p, const float* rf, int n_scat, const float* amps,
+                        float* out, cudaStream_t st) {
+    const size_t row_len = (size_t)p.n_elem * p.n_samples;
+    const int grid = (int)std::min<size_t>((row_len + 255) / 256, (size_t)152 * 8);
+    line_combine_kernel<<<grid, 256, sizeof(int) * (size_t)n_scat, st>>>(n_scat, row_len, rf, amps,
+                                                                        out);
+    return check_launch("line_combine_kernel");
+}
+
+int launch_line_model(const tidas_line_params& p, const float* S, int s, const float* theta,
+                      double eps, float* out, cudaStream_t st) {
+    const line::Dev L = line_dev(p);
+    line_model_kernel<<<(L.D + 7) / 8, 256, 0, st>>>(L, S, s, theta, eps, out);
+    return check_launch("line_model_kernel");
+}
+
+int launch_line_envelope(int n_rows, int n, const float* x, float* env, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (((size_t)n + 1) & ~(size_t)1) + sizeof(float2) * (size_t)n;
+    if (smem > 220 * 1024)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "line envelope: rows of %d points do not fit", n);
+    cudaFuncSetAttribute(line_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    line_envelope_kernel<<<n_rows, 256, smem, st>>>(n, x, env);
+    return check_launch("line_envelope_kernel");
+}
 }  // namespace tidas

@@ -235,3 +235,32 @@ class LineExperiment:
         capi.tidas_line_sweep(self.P, _ptr(rf), _ptr(lines), r_first, n, float(eps),
                               *[_ptr(o) for o in outs], _stream())
         return tuple(outs)
+
+    def combine(self, rf, amps, out=None):
+        """Channel data of a line of scatterers, amps[r] on point r."""
+        n = rf.shape[0]
+        _need(rf, torch.float32, (n, self.N, self.S), "rf")
+        _need(amps, torch.float32, (n,), "amps")
+        out = out if out is not None else torch.empty((self.N, self.S), dtype=torch.float32,
+                                                      device=rf.device)
+        capi.tidas_line_combine(self.P, _ptr(rf), n, _ptr(amps), _ptr(out), _stream())
+        return out
+
+    def model(self, rf_line, s, theta, eps, out=None):
+        """Eq. (2.13): the line model with delay curve s and weights theta."""
+        _need(rf_line, torch.float32, (self.N, self.S), "rf_line")
+        _need(theta, torch.float32, (self.D,), "theta")
+        out = out if out is not None else torch.empty((self.D,), dtype=torch.float32,
+                                                      device=rf_line.device)
+        capi.tidas_line_model(self.P, _ptr(rf_line), int(s), _ptr(theta), float(eps), _ptr(out),
+                              _stream())
+        return out
+
+
+def envelope(x, out=None):
+    """Envelope of each row of x [rows, n] (modulus of the analytic signal)."""
+    x2 = x.reshape(-1, x.shape[-1])
+    _need(x2, torch.float32, tuple(x2.shape), "x")
+    out = out if out is not None else torch.empty_like(x2)
+    capi.tidas_line_envelope(x2.shape[0], x2.shape[1], _ptr(x2), _ptr(out), _stream())
+    return out.reshape(x.shape)

@@ -132,3 +132,51 @@ def test_paper_line_600_by_600_sampled_pairs():
     _compare_sweep(O, rf_h, g_h, th, el, eg, rs, (0, 10, 100, 300, 343, 344, 345, 598, 599), eps)
     np.testing.assert_allclose(np.diag(th), 1.0, rtol=1e-6)
     assert np.all(np.isfinite(th)) and np.all(el >= 0) and np.all(eg >= -1e-6)
+
+
+# ------------------------------------------------------ line reconstruction
+def test_line_data_and_model_match_oracle():
+    p = small_params()
+    E, O = experiment(p), line_oracle(p)
+    rf = E.synthesize()
+    amps = np.zeros(41, np.float32)
+    amps[[6, 19, 31]] = [1.0, -0.7, 2.5]
+    S = E.combine(rf, to_dev(amps))
+    S_h = host(S)
+    assert rel_l2(S_h, O.line_data(amps.astype(np.float64))) <= 1e-5
+    eps = O.eps()
+    rng = np.random.default_rng(7)
+    for s in (5, 20, 35):
+        th = rng.uniform(0.5, 2.0, 41).astype(np.float32)
+        got = host(E.model(S, s, to_dev(th), eps))
+        ref = O.model_line(S_h.astype(np.float64), s, th.astype(np.float64), eps)
+        assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [600, 41, 257])
+def test_envelope_matches_oracle(n):
+    from oracle.line import envelope as env_ref
+    from paper_2507_15464_gb300.ops import envelope
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((3, n)).astype(np.float32)
+    k = np.arange(n)
+    x[1] = (np.exp(-((k - n / 2) / (n / 12)) ** 2) * np.cos(2 * np.pi * 0.23 * k)).astype(np.float32)
+    got = host(envelope(to_dev(x)))
+    for j in range(3):
+        assert rel_l2(got[j], env_ref(x[j].astype(np.float64))) <= 1e-5
+
+
+def test_paper_line_reconstruction_matches_oracle():
+    # five unit scatterers, delay curve of the 25 mm point, theta from the sweep
+    from oracle.line import line_scenarios
+    p, O, rf_h, g_h, th, el, eg, eps = _paper_run()
+    E = experiment(p)
+    s = int(np.argmin(np.abs(O.depths() - 25e-3)))
+    amps = line_scenarios()["5_uniform"].astype(np.float32)
+    rf = to_dev(rf_h)
+    S = E.combine(rf, to_dev(amps))
+    S_h = host(S).astype(np.float64)
+    das = host(E.das_lines(S.reshape(1, *S.shape)))[0]
+    assert rel_l2(das, O.das_line(S_h)) <= 1e-5
+    got = host(E.model(S, s, to_dev(np.ascontiguousarray(th[s])), eps))
+    assert rel_l2(got, O.model_line(S_h, s, th[s].astype(np.float64), eps)) <= 1e-5

@@ -126,3 +126,53 @@ def test_errors_are_relative_energies_of_the_difference():
     # the local points are the scatterer's own neighbourhood in depth
     w = O.local_points(r, eps)
     assert w[r] and w.sum() >= 1 and np.all(np.abs(np.nonzero(w)[0] - r) <= 1)
+
+
+def test_line_model_at_a_scatterer_is_its_windowed_fixed_curve_line():
+    # Eq. (2.13) with theta = 1 on the data of one scatterer r reads, at point
+    # r, the windowed fixed-curve line of Eq. (2.8) for that scatterer
+    O = small_line()
+    eps = O.eps()
+    for r, s in ((12, 12), (12, 16), (30, 25)):
+        S = O.synth(r)
+        m = O.model_line(S, s, np.ones(41), eps)
+        assert m[r] == pytest.approx(O.fixed_line(S, r, s, eps)[r], rel=1e-12, abs=1e-15)
+
+
+def test_line_model_is_linear_and_scaled_by_theta():
+    O = small_line()
+    eps = O.eps()
+    amps = np.zeros(41)
+    amps[[8, 22]] = [1.0, -0.5]
+    S = O.line_data(amps)
+    np.testing.assert_allclose(S, O.synth(8) - 0.5 * O.synth(22), rtol=0, atol=1e-12)
+    th = np.linspace(0.5, 2.0, 41)
+    m = O.model_line(S, 20, th, eps)
+    m1 = O.model_line(O.synth(8), 20, np.ones(41), eps)
+    m2 = O.model_line(O.synth(22), 20, np.ones(41), eps)
+    np.testing.assert_allclose(m, th * (m1 - 0.5 * m2), rtol=1e-12, atol=1e-14)
+
+
+def test_envelope_of_pure_and_modulated_tones():
+    from oracle.line import envelope
+    n = 600
+    k = np.arange(n)
+    np.testing.assert_allclose(envelope(np.cos(2 * np.pi * 37 * k / n + 0.3)), 1.0, atol=1e-12)
+    # a narrow-band Gaussian burst: the envelope is the Gaussian
+    g = np.exp(-((k - 300) / 40.0) ** 2)
+    np.testing.assert_allclose(envelope(g * np.cos(2 * np.pi * 0.2 * k)), g, atol=1e-6)
+
+
+def test_sidelobe_level_and_main_lobes():
+    from oracle.line import line_scenarios, sidelobe_level_db
+    z = np.arange(100) * 1e-4
+    env = np.full(100, 0.1)
+    env[[20, 60]] = 1.0
+    assert sidelobe_level_db(env, z, [20, 60], 2.5e-4) == pytest.approx(-20.0, abs=1e-12)
+    sc = line_scenarios()
+    assert (sc["5_uniform"] > 0).sum() == 5 and (sc["100_uniform"] > 0).sum() == 100
+    np.testing.assert_array_equal(np.nonzero(sc["5_increasing"])[0], np.nonzero(sc["5_uniform"])[0])
+    O = LineOracle(paper_line())
+    # main lobe: the pulse envelope 20 dB down, two-way depth
+    t20 = O.mainlobe_halfwidth() * 2 / 1540.0
+    assert np.exp(-O.alpha() * t20 ** 2) == pytest.approx(0.1, rel=1e-12)
