@@ -137,6 +137,56 @@ class DasPlan:
         return k
 
 
+class DasStreamer:
+    """Host batches through das_forward with the transfers overlapped.
+
+    Two device batch buffers: while batch k is beamformed on the compute
+    stream, batch k + 1 is uploaded on an upload stream and batch k - 1's
+    image is read back on a download stream.  Every batch still makes its
+    own host -> device and device -> host copy; events order the reuse of
+    each buffer.  There is a single compute stream, so the plan's staging
+    buffer serves one batch at a time.  Destroying a plan synchronises the
+    device (cudaFree), which drains the pipeline: keep plan lifetimes (and
+    the garbage collector) out of the submission loop."""
+
+    def __init__(self, plan: DasPlan, n_frames: int, device="cuda"):
+        self.plan = plan
+        self.rf = [torch.empty(plan.rf_shape(n_frames), dtype=plan.rf_dtype, device=device)
+                   for _ in range(2)]
+        self.img = [torch.empty(plan.img_shape(n_frames), dtype=torch.float32, device=device)
+                    for _ in range(2)]
+        self.up, self.comp, self.down = (torch.cuda.Stream() for _ in range(3))
+        self.uploaded = [torch.cuda.Event() for _ in range(2)]
+        self.computed = [torch.cuda.Event() for _ in range(2)]
+        self.downloaded = [torch.cuda.Event() for _ in range(2)]
+        self.used = [False, False]
+        self.k = 0
+
+    def submit(self, host_rf, host_img):
+        """Queue one batch (pinned host tensors).  Returns the event after
+        which host_img holds its image."""
+        b = self.k & 1
+        reuse = self.used[b]
+        with torch.cuda.stream(self.up):
+            if reuse:
+                self.up.wait_event(self.computed[b])  # batch k - 2 has read rf[b]
+            self.rf[b].copy_(host_rf, non_blocking=True)
+            self.uploaded[b].record(self.up)
+        with torch.cuda.stream(self.comp):
+            self.comp.wait_event(self.uploaded[b])
+            if reuse:
+                self.comp.wait_event(self.downloaded[b])  # img[b] of batch k - 2 is out
+            self.plan.forward(self.rf[b], out=self.img[b])
+            self.computed[b].record(self.comp)
+        with torch.cuda.stream(self.down):
+            self.down.wait_event(self.computed[b])
+            host_img.copy_(self.img[b], non_blocking=True)
+            self.downloaded[b].record(self.down)
+        self.used[b] = True
+        self.k += 1
+        return self.downloaded[b]
+
+
 def _tidas(fn, kernels, x, variant, out=None):
     nz, taps = kernels.shape
     nf, nz2, nx = x.shape

@@ -266,3 +266,21 @@ def test_fit_kernels_compound_sampled_rows():
     rows = list(range(0, 1024, 97)) + [1023]
     ref = O.psf_rows(63, rows=rows)
     assert rel_l2(k[rows], ref) <= TOL32
+
+
+def test_streamer_overlapped_batches_equal_plain_forward():
+    # the serving form: uploads / read-backs overlap the beamforming on
+    # separate streams; every image equals the plain call on the same batch
+    from paper_2507_15464_gb300.ops import DasStreamer
+    g = presets.geometry("pw64_single", nz=64, z0=10e-3)
+    P = plan(g, torch.float16)
+    nf = 16
+    batches = [torch.from_numpy(generators.standard_normal(P.rf_shape(nf), (50 + k,), np.float32))
+               .to(torch.float16).pin_memory() for k in range(5)]
+    outs = [torch.empty(P.img_shape(nf), dtype=torch.float32).pin_memory() for _ in range(5)]
+    S = DasStreamer(P, nf)
+    done = [S.submit(b, o) for b, o in zip(batches, outs)]
+    done[-1].synchronize()
+    torch.cuda.synchronize()
+    for b, o in zip(batches, outs):
+        np.testing.assert_array_equal(o.numpy(), host(P.forward(b.cuda())))
