@@ -402,8 +402,133 @@ __global__ void __launch_bounds__(256) synth_grid_kernel(DasDev d, const float* 
     for (int k = threadIdx.x; k < S; k += blockDim.x) out[k] = acc[k];
 }
 
+// Gather form of the same sum, used for the grid: each thread owns kGS
+// consecutive samples of the channel row and adds, column by column, the
+// pixels whose pulse reaches them.  The delay grows with depth down a
+// column (d/dz of x sin + z cos + |r - x_n| is cos + z / |r - x_n| > 0), so
+// those pixels are a contiguous run found by binary search over the
+// column's integer delays.  Per (pixel, thread) the pulse is evaluated
+// exactly at the thread's first sample and carried over its kGS samples by
+// recurrences (envelope ratio exp(-beta (2 t + 1)), carrier rotation).  No
+// atomics; each sample is summed in a fixed order (columns, then depth).
+constexpr int kGS = 16;
+__global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
+                                                                const float* __restrict__ reflT,
+                                                                float* __restrict__ rf) {
+    extern __shared__ float sm[];
+    const int NZ = d.nz, NX = d.nx, S = d.n_samples;
+    int* ui = reinterpret_cast<int*>(sm);  // [NZ] integer delay of the column's pixels
+    float* uf = sm + NZ;                   // [NZ] fraction
+    float* vz = uf + NZ;                   // [NZ] reflectivity of the column
+    const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
+    const float* rt = reflT + (size_t)f * NX * NZ;
+    const int hi_tap = (int)ceilf(d.thalf) + 1;
+    // constant recurrence factors: exp(-2 beta) and the carrier's rotation by one sample
+    const float h = expf(-2.f * d.beta);
+    float sw, cw;
+    sincospif(d.wcar, &sw, &cw);
+    float* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
+    for (int base = 0; base < S; base += kGS * (int)blockDim.x) {
+        const int k0 = base + kGS * (int)threadIdx.x;
+        float acc[kGS];
+#pragma unroll
+        for (int q = 0; q < kGS; ++q) acc[q] = 0.f;
+        for (int ix = 0; ix < NX; ++ix) {
+            __syncthreads();
+            const float dxs = __ldg(d.dxs + (size_t)n * NX + ix);
+            for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+                int i;
+                float phi;
+                pixel_delay(d, a, ix, iz, rx_excess(dxs, __ldg(d.zs + iz)), i, phi);
+                ui[iz] = i;
+                uf[iz] = phi;
+                vz[iz] = __ldg(rt + (size_t)ix * NZ + iz);
+            }
+            __syncthreads();
+            if (k0 >= S) continue;
+            // first pixel with i >= k0 - hi_tap, last with i <= k0 + kGS - 1 + hi_tap
+            int lo = 0, hi = NZ;
+            const int want_lo = k0 - hi_tap;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ui[mid] < want_lo) lo = mid + 1; else hi = mid;
+            }
+            int lo2 = lo, hi2 = NZ;
+            const int want_hi = k0 + kGS - 1 + hi_tap;
+            while (lo2 < hi2) {
+                const int mid = (lo2 + hi2) >> 1;
+                if (ui[mid] <= want_hi) lo2 = mid + 1; else hi2 = mid;
+            }
+            for (int iz = lo; iz < lo2; ++iz) {
+                const float v = vz[iz];
+                if (v == 0.f) continue;
+                const int i = ui[iz];
+                const float phi = uf[iz];
+                const int jlo = (int)ceilf(phi - d.thalf), jhi = (int)floorf(phi + d.thalf);
+                const int j0 = k0 - i;  // tap index of this thread's first sample
+                const float t0 = (float)j0 - phi;
+                float e = v * expf(-d.beta * t0 * t0);
+                float r = expf(-d.beta * (2.f * t0 + 1.f));
+                float sn, cs;
+                sincospif(d.wcar * t0, &sn, &cs);
+#pragma unroll
+                for (int q = 0; q < kGS; ++q) {
+                    const int j = j0 + q;
+                    if (j >= jlo && j <= jhi) acc[q] = fmaf(e, cs, acc[q]);
+                    e *= r;
+                    r *= h;
+                    const float c2 = cs * cw - sn * sw;
+                    sn = fmaf(sn, cw, cs * sw);
+                    cs = c2;
+                }
+            }
+        }
+        if (k0 < S) {
+#pragma unroll
+            for (int q = 0; q < kGS; ++q)
+                if (k0 + q < S) out[k0 + q] = acc[q];
+        }
+    }
+}
+
+// refl [nf][nz][nx] -> reflT [nf][nx][nz], 32 x 32 tiles through shared memory
+__global__ void transpose_grid_kernel(const float* __restrict__ in, float* __restrict__ out, int nz,
+                                      int nx) {
+    __shared__ float tile[32][33];
+    const int f = blockIdx.z;
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+    const float* src = in + (size_t)f * nz * nx;
+    float* dst = out + (size_t)f * nz * nx;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int z = z0 + j, x = x0 + threadIdx.x;
+        tile[j][threadIdx.x] = (z < nz && x < nx) ? src[(size_t)z * nx + x] : 0.f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int x = x0 + j, z = z0 + threadIdx.x;
+        if (x < nx && z < nz) dst[(size_t)x * nz + z] = tile[threadIdx.x][j];
+    }
+}
+
 int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, cudaStream_t st) {
     const DasDev& d = P.dev;
+    const size_t smem_g = (size_t)3 * d.nz * sizeof(float);
+    if (smem_g <= 200 * 1024) {
+        float* reflT = nullptr;
+        TIDAS_CUDA(cudaMallocAsync((void**)&reflT, sizeof(float) * (size_t)nf * d.nz * d.nx, st));
+        transpose_grid_kernel<<<dim3((d.nx + 31) / 32, (d.nz + 31) / 32, nf), dim3(32, 8), 0, st>>>(
+            refl, reflT, d.nz, d.nx);
+        int rc = check_launch("transpose_grid_kernel");
+        if (rc == TIDAS_OK) {
+            cudaFuncSetAttribute(synth_grid_gather_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+            synth_grid_gather_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem_g, st>>>(d, reflT,
+                                                                                        rf);
+            rc = check_launch("synth_grid_gather_kernel");
+        }
+        cudaFreeAsync(reflT, st);
+        return rc;
+    }
     size_t smem = (size_t)d.n_samples * sizeof(float);
     cudaFuncSetAttribute(synth_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     synth_grid_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem, st>>>(d, refl, rf);
