@@ -372,6 +372,13 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         int pos = 0, j = 0;  // first chunk of pair j in the ring
         bool first = true, bad = false;
         for (int q = grp; q < npairs; q += kGroups, ++j) {
+            // Pair j - 1's MMAs must be complete before this barrier: past it the
+            // builders write pair j + 1 into the tile pair j - 1 read.  (Its MMAs
+            // ran while the builders wrote pair j, so this rarely waits.)
+            if (lane == 0 && j >= 1 && !bad)
+                bad = !mbar_wait_or_abort(&gempty[(j - 1) % kPairSlots],
+                                          (uint32_t)((j - 1) / kPairSlots) & 1u, s_abort,
+                                          &g_das_tc_wait_error, 304);
             // the group's weight tile of pair q is written (leave together on an abort)
             if (group_bar(grp, bad || *s_abort)) break;
             const int steps = s_tab[q] & 7;
@@ -413,7 +420,6 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         const bool valid = ix < d.nx && iz < d.nz;
         const int ixc = valid ? ix : 0, izc = valid ? iz : 0;
         const float zs = __ldg(d.zs + izc);
-        uint64_t* gempty = empty + grp * kPairSlots;
         uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
         const int swz = m & 7;
         float w = 0.f, exc = 0.f;
@@ -437,11 +443,8 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             const int st = q & (kWTiles - 1);
             const int e = s_tab[q];
             const int k0 = e & ~7, steps = e & 7;
-            // the tile was last read by this group's pair j - 2
-            if (j >= 2)
-                bad = bad || !mbar_wait_or_abort(&gempty[(j - 2) % kPairSlots],
-                                                 (uint32_t)((j - 2) / kPairSlots) & 1u, s_abort,
-                                                 &g_das_tc_wait_error, 304);
+            // the tile was last read by this group's pair j - 2, whose MMAs the
+            // MMA warp saw complete before the previous group barrier
             if (!bad) {
                 uint8_t* W = rowp + st * kWBytes;
                 const int pc = prev[st * kM + m];
