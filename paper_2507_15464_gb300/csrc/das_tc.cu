@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     uint32_t* tmem_slot = (uint32_t*)(done + kGroups);
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
     int* s_used = (int*)(tmem_slot + 2);                       // [kGroups]
-    int8_t* prev = (int8_t*)((uint8_t*)full + 1024);           // [kWTiles][kM]
+    int8_t* prev = (int8_t*)((uint8_t*)full + 1024);           // [kWTiles][kM] (unused slot)
     int2* s_base = (int2*)(prev + kWTiles * kM);               // [A][kM]: transmit split
     int16_t* s_tab = (int16_t*)(s_base + A * kM);              // [pair]: window entries
 
@@ -275,7 +275,6 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     // zero the weight tiles once; afterwards only written chunks are erased
     for (int i = threadIdx.x; i < kWTiles * kWBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(sW)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = threadIdx.x; i < kWTiles * kM; i += blockDim.x) prev[i] = -1;
     // this tile's window entries (pair order: element-major, angle-minor) and
     // the transmit split of its pixels, so that no role waits on a global load
     // per pair
@@ -423,6 +422,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
         const int swz = m & 7;
         float w = 0.f, exc = 0.f;
+        int prev_a = -1, prev_b = -1;
         int cur_n = -1;
         int n = n_lo + grp / A, a = grp % A;
         // lateral offset of the group's next element, loaded one element ahead
@@ -447,7 +447,9 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             // MMA warp saw complete before the previous group barrier
             if (!bad) {
                 uint8_t* W = rowp + st * kWBytes;
-                const int pc = prev[st * kM + m];
+                // column of the chunk this thread last wrote into this tile (-1: none);
+                // the group's two tiles alternate with j
+                const int pc = (j & 1) ? prev_b : prev_a;
                 if (pc >= 0) {
                     *reinterpret_cast<uint4*>(W + (((pc >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
                     if ((pc & 7) > 4)
@@ -488,7 +490,10 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                         nc = c;
                     }
                 }
-                prev[st * kM + m] = (int8_t)nc;
+                if (j & 1)
+                    prev_b = nc;
+                else
+                    prev_a = nc;
             }
             fence_proxy_async_smem();
             if (group_bar(grp, bad || *s_abort)) break;
