@@ -418,7 +418,7 @@ def bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak, bf
     d = das_img[0].double()
     res["nrmse_vs_exact_das"] = float((out[0].double() - d).norm() / d.norm())
     res["band_2d"] = bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, d, args, stream,
-                                   bf16_peak)
+                                   bf16_peak, das_ms_per_frame)
     return res
 
 
@@ -435,7 +435,8 @@ def _band_rows_oracle(kern, x, rows):
     return np.stack(out, axis=1)
 
 
-def bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, das0, args, stream, bf16_peak):
+def bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, das0, args, stream, bf16_peak,
+                  das_ms_per_frame):
     """2D band kernels (KZ x TAPS per depth row) on the same 256-frame batch:
     kernel fit, direct FP32 and tcgen05 Toeplitz GEMM forward maps, accuracy
     against the oracle and against the exact DAS image."""
@@ -468,7 +469,8 @@ def bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, das0, args, stream,
             continue
         m = time_steps(torch, fn, max(3, args.steps), 2, stream)
         r = {"ms": m, "mpix_s": nf * nz * nx / (m * 1e-3) / 1e6,
-             "useful_tflops": useful / (m * 1e-3) / 1e12}
+             "useful_tflops": useful / (m * 1e-3) / 1e12,
+             "speedup_vs_das_per_frame": das_ms_per_frame / (m / nf)}
         if variant == capi.VARIANT_GEMM_BF16:
             a = mma / (m * 1e-3) / 1e12
             # the call is the operand repack plus the GEMM; both are in `ms`
