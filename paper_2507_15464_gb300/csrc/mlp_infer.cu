@@ -2,13 +2,16 @@
 // layers of the 4 -> 256 -> 256 -> 256 -> 63 MLP for a tile of 128 samples,
 // without writing hidden activations to global memory.
 //
-// Persistent: one CTA per SM walks 128-row tiles.  Per tile the epilogue
-// warps encode the samples into the first layer's operand, and after each
-// layer read the FP32 accumulator from tensor memory, add the bias, apply
-// ReLU and write the BF16 activations back into shared memory (128-byte
-// swizzled, K-major: the next layer's A operand).  The weights, identical for
-// every tile, stream from L2 by TMA in 64-column chunks through a ring that
-// runs across layers and tiles.  Roles: warp 0 loads weights (and owns tensor
+// Persistent: one CTA per SM walks 128-row tiles, two at a time.  Per tile
+// the epilogue warps encode the samples into the first layer's operand, and
+// after each layer read the FP32 accumulator from tensor memory, add the
+// bias, apply ReLU and write the BF16 activations back into shared memory
+// (128-byte swizzled, K-major: the next layer's A operand).  The two tiles of
+// a round have their own operands and accumulators and take the layers in
+// turn (layer l of tile 0, layer l of tile 1, layer l + 1 of tile 0, ...), so
+// one tile's epilogue runs while the other's MMAs do.  The weights, identical
+// for every tile, stream from L2 by TMA in 64-column chunks through a ring,
+// in the order the MMAs consume them.  Roles: warp 0 loads weights (and owns tensor
 // memory), warp 1 issues the MMAs, warps 2-5 run encode and epilogues (one
 // accumulator row per thread).  The last layer's output is scaled per row
 // (the apodization sum) and stored in FP32.
@@ -32,14 +35,16 @@ constexpr int kM = 128;       // samples per tile (UMMA M)
 constexpr int kHid = 256;
 constexpr int kIO = 64;       // padded input / output width
 constexpr int kKC = 64;       // K columns per weight chunk / activation chunk
-constexpr int kStages = 3;    // weight chunks in flight
+constexpr int kStages = 2;    // weight chunks in flight
+constexpr int kTiles = 2;     // tiles per round (ping-pong)
 constexpr int kWBytes = kHid * kKC * 2;   // 32 KB (largest chunk)
 constexpr int kABytes = kM * kKC * 2;     // 16 KB per activation chunk
 constexpr int kAChunks = kHid / kKC;      // 4
 constexpr int kChunksPerTile = 1 + 3 * kAChunks;  // W1, W2 x4, W3 x4, W4 x4
 constexpr int kBias = 3 * kHid + kIO;
-constexpr size_t kSmem = 1024 + (size_t)kStages * kWBytes + (size_t)kAChunks * kABytes + 1024 +
-                         (size_t)kBias * 4;
+constexpr size_t kSmem = 1024 + (size_t)kStages * kWBytes + (size_t)kTiles * kAChunks * kABytes +
+                         1024 + (size_t)kBias * 4;
+static_assert(kSmem <= 227 * 1024, "shared memory");
 // weight chunk q of a tile: layer and K offset
 __host__ __device__ constexpr int chunk_layer(int q) { return q == 0 ? 0 : 1 + (q - 1) / kAChunks; }
 __host__ __device__ constexpr int chunk_k(int q) { return q == 0 ? 0 : ((q - 1) % kAChunks) * kKC; }
@@ -60,12 +65,12 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sW = base;                                  // [kStages] weight chunks
-    uint8_t* sA = sW + kStages * kWBytes;                // [kAChunks] activation chunks
-    uint64_t* full = (uint64_t*)(sA + kAChunks * kABytes);
+    uint8_t* sA = sW + kStages * kWBytes;                // [kTiles][kAChunks] activation chunks
+    uint64_t* full = (uint64_t*)(sA + kTiles * kAChunks * kABytes);
     uint64_t* empty = full + kStages;
-    uint64_t* a_full = empty + kStages;   // epilogue -> MMA: operand written, accumulator read
-    uint64_t* acc_full = a_full + 1;      // MMA -> epilogue: layer done
-    uint64_t* done = acc_full + 1;
+    uint64_t* a_full = empty + kStages;   // [kTiles] epilogue -> MMA: operand written, accumulator read
+    uint64_t* acc_full = a_full + kTiles; // [kTiles] MMA -> epilogue: layer done
+    uint64_t* done = acc_full + kTiles;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
     float* s_bias = (float*)((uint8_t*)full + 1024);     // b1 | b2 | b3 | b4
@@ -78,8 +83,10 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(a_full, 4);
-        mbar_init(acc_full, 1);
+        for (int b = 0; b < kTiles; ++b) {
+            mbar_init(&a_full[b], 4);
+            mbar_init(&acc_full[b], 1);
+        }
         mbar_init(done, 1);
         *s_abort = 0;
         fence_barrier_init();
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(192, 1)
         s_bias[i] = i < kHid ? b1[i] : i < 2 * kHid ? b2[i - kHid] : i < 3 * kHid ? b3[i - 2 * kHid]
                                                                               : b4[i - 3 * kHid];
     if (warp == 0) {
-        tmem_alloc(tmem_slot, kHid);
+        tmem_alloc(tmem_slot, kTiles * kHid);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -104,11 +111,14 @@ __global__ void __launch_bounds__(192, 1)
         // ------------------------------------------------ weight chunks by TMA
         if (lane == 0) {
             uint32_t st = 0, ph = 0;
-            for (int t = blockIdx.x; t < ntiles && !*s_abort; t += gridDim.x) {
-                for (int q = 0; q < kChunksPerTile; ++q) {
+            for (int t = blockIdx.x; t < ntiles && !*s_abort; t += kTiles * gridDim.x) {
+                const int nt = (t + (int)gridDim.x < ntiles) ? kTiles : 1;  // tiles this round
+                for (int qi = 0; qi < nt * kChunksPerTile; ++qi) {
+                    // layer l's chunks for tile 0, then for tile 1
+                    const int l = qi == 0 ? 0 : (qi < nt ? 0 : 1 + (qi - nt) / (nt * kAChunks));
+                    const int q = l == 0 ? 0 : 1 + (l - 1) * kAChunks + (qi - nt) % kAChunks;
                     if (!mbar_wait_or_abort(&empty[st], ph ^ 1u, s_abort, &g_mlp_infer_wait_error, 401))
                         break;
-                    const int l = chunk_layer(q);
                     const CUtensorMap* map = l == 0 ? &w1 : l == 1 ? &w2 : l == 2 ? &w3 : &w4;
                     const uint32_t bytes = (l == 3 ? kIO : kHid) * kKC * 2;
                     mbar_arrive_expect_tx(&full[st], bytes);
@@ -127,29 +137,33 @@ __global__ void __launch_bounds__(192, 1)
         // ------------------------------------------------------------- MMAs
         if (lane == 0) {
             const uint32_t id_h = idesc_bf16_f32(kM, kHid), id_o = idesc_bf16_f32(kM, kIO);
-            uint32_t st = 0, ph = 0, aph = 0;
+            uint32_t st = 0, ph = 0, aph[kTiles] = {0, 0};
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                int q = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += kTiles * gridDim.x) {
+                const int nt = (t + (int)gridDim.x < ntiles) ? kTiles : 1;
                 for (int l = 0; l < 4 && ok; ++l) {
-                    ok = mbar_wait_or_abort(a_full, aph, s_abort, &g_mlp_infer_wait_error, 402);
-                    aph ^= 1u;
-                    if (!ok) break;
-                    tc_fence_after();
-                    const int nchunks = l == 0 ? 1 : kAChunks;
-                    for (int c = 0; c < nchunks; ++c, ++q) {
-                        ok = mbar_wait_or_abort(&full[st], ph, s_abort, &g_mlp_infer_wait_error, 403);
+                    for (int b = 0; b < nt && ok; ++b) {
+                        ok = mbar_wait_or_abort(&a_full[b], aph[b], s_abort, &g_mlp_infer_wait_error, 402);
+                        aph[b] ^= 1u;
                         if (!ok) break;
                         tc_fence_after();
-                        const uint32_t a = smem_u32(sA + c * kABytes), b = smem_u32(sW + st * kWBytes);
+                        const uint32_t acc = tmem + (uint32_t)(b * kHid);
+                        const uint8_t* ab = sA + (size_t)b * kAChunks * kABytes;
+                        const int nchunks = l == 0 ? 1 : kAChunks;
+                        for (int c = 0; c < nchunks; ++c) {
+                            ok = mbar_wait_or_abort(&full[st], ph, s_abort, &g_mlp_infer_wait_error, 403);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint32_t a = smem_u32(ab + c * kABytes), w = smem_u32(sW + st * kWBytes);
 #pragma unroll
-                        for (int kk = 0; kk < kKC / 16; ++kk)
-                            mma_f16(tmem, desc_sw128_kmajor(a) + 2 * kk, desc_sw128_kmajor(b) + 2 * kk,
-                                    l == 3 ? id_o : id_h, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_commit(&empty[st]);
-                        if (++st == kStages) { st = 0; ph ^= 1; }
+                            for (int kk = 0; kk < kKC / 16; ++kk)
+                                mma_f16(acc, desc_sw128_kmajor(a) + 2 * kk, desc_sw128_kmajor(w) + 2 * kk,
+                                        l == 3 ? id_o : id_h, (c > 0 || kk > 0) ? 1u : 0u);
+                            mma_commit(&empty[st]);
+                            if (++st == kStages) { st = 0; ph ^= 1; }
+                        }
+                        if (ok) mma_commit(&acc_full[b]);
                     }
-                    mma_commit(acc_full);
                 }
             }
             mma_commit(done);
@@ -161,14 +175,15 @@ __global__ void __launch_bounds__(192, 1)
         const int q4 = warp & 3;                          // tensor-memory lane quadrant
         const int r = 32 * q4 + lane;                     // row of the tile
         const uint32_t lane_base = (uint32_t)(32 * q4) << 16;
-        uint8_t* const arow = sA + (r >> 3) * 1024 + (r & 7) * 128;  // row in each chunk
         const int swz = r & 7;
-        uint32_t cph = 0;
+        uint32_t cph[kTiles] = {0, 0};
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int row = t * kM + r;
+        for (int t = blockIdx.x; t < ntiles && ok; t += kTiles * gridDim.x) {
+            const int nt = (t + (int)gridDim.x < ntiles) ? kTiles : 1;
             // encode: four features in [-1, 1], zeros in columns 4..63
-            {
+            for (int b = 0; b < nt; ++b) {
+                const int row = (t + b * (int)gridDim.x) * kM + r;
+                uint8_t* const arow = sA + (size_t)b * kAChunks * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
                 uint4 v = make_uint4(0, 0, 0, 0);
                 if (row < n) {
                     float f[4];
@@ -185,64 +200,71 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int u = 1; u < 8; ++u)
                     *reinterpret_cast<uint4*>(arow + ((u ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&a_full[b]);
             }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(a_full);
-            for (int l = 0; l < 4; ++l) {
-                ok = mbar_wait_or_abort(acc_full, cph, s_abort, &g_mlp_infer_wait_error, 405);
-                cph ^= 1u;
-                if (!ok) break;
-                tc_fence_after();
-                if (l < 3) {
-                    // bias, ReLU, BF16 into the next layer's operand
-                    const float* bl = s_bias + l * kHid;
+            for (int l = 0; l < 4 && ok; ++l) {
+                for (int b = 0; b < nt && ok; ++b) {
+                    const int row = (t + b * (int)gridDim.x) * kM + r;
+                    uint8_t* const arow = sA + (size_t)b * kAChunks * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
+                    const uint32_t acc_col = (uint32_t)(b * kHid);
+                    ok = mbar_wait_or_abort(&acc_full[b], cph[b], s_abort, &g_mlp_infer_wait_error, 405);
+                    cph[b] ^= 1u;
+                    if (!ok) break;
+                    tc_fence_after();
+                    if (l < 3) {
+                        // bias, ReLU, BF16 into the next layer's operand
+                        const float* bl = s_bias + l * kHid;
 #pragma unroll 1
-                    for (int j = 0; j < kHid; j += 32) {
-                        uint32_t acc[32];
-                        tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)j, acc);
-                        tmem_ld_wait();
-                        uint32_t pk[16];
+                        for (int j = 0; j < kHid; j += 32) {
+                            uint32_t acc[32];
+                            tmem_ld_32x32b_x32(tmem + lane_base + acc_col + (uint32_t)j, acc);
+                            tmem_ld_wait();
+                            uint32_t pk[16];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const float x0 = fmaxf(__uint_as_float(acc[2 * e]) + bl[j + 2 * e], 0.f);
-                            const float x1 = fmaxf(__uint_as_float(acc[2 * e + 1]) + bl[j + 2 * e + 1], 0.f);
-                            const __nv_bfloat162 p = __floats2bfloat162_rn(x0, x1);
-                            pk[e] = *reinterpret_cast<const uint32_t*>(&p);
-                        }
-                        uint8_t* chunk = arow + (j / kKC) * kABytes;
+                            for (int e = 0; e < 16; ++e) {
+                                const float x0 = fmaxf(__uint_as_float(acc[2 * e]) + bl[j + 2 * e], 0.f);
+                                const float x1 = fmaxf(__uint_as_float(acc[2 * e + 1]) + bl[j + 2 * e + 1], 0.f);
+                                const __nv_bfloat162 p = __floats2bfloat162_rn(x0, x1);
+                                pk[e] = *reinterpret_cast<const uint32_t*>(&p);
+                            }
+                            uint8_t* chunk = arow + (j / kKC) * kABytes;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int unit = ((j % kKC) >> 3) + u;
-                            *reinterpret_cast<uint4*>(chunk + ((unit ^ swz) << 4)) =
-                                make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+                            for (int u = 0; u < 4; ++u) {
+                                const int unit = ((j % kKC) >> 3) + u;
+                                *reinterpret_cast<uint4*>(chunk + ((unit ^ swz) << 4)) =
+                                    make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+                            }
                         }
-                    }
-                    fence_proxy_async_smem();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(a_full);
-                } else {
-                    // output layer: bias, apodization scale, FP32 store
-                    const float* bl = s_bias + 3 * kHid;
-                    const float sc = (row < n && scale) ? scale[row] : 1.f;
+                        fence_proxy_async_smem();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&a_full[b]);
+                    } else {
+                        // output layer: bias, apodization scale, FP32 store
+                        const float* bl = s_bias + 3 * kHid;
+                        const float sc = (row < n && scale) ? scale[row] : 1.f;
 #pragma unroll 1
-                    for (int j = 0; j < kIO; j += 32) {
-                        uint32_t acc[32];
-                        tmem_ld_32x32b_x32(tmem + lane_base + (uint32_t)j, acc);
-                        tmem_ld_wait();
-                        if (row < n) {
-                            float4* dst = reinterpret_cast<float4*>(out + (size_t)row * ldo + j);
+                        for (int j = 0; j < kIO; j += 32) {
+                            uint32_t acc[32];
+                            tmem_ld_32x32b_x32(tmem + lane_base + acc_col + (uint32_t)j, acc);
+                            tmem_ld_wait();
+                            if (row < n) {
+                                float4* dst = reinterpret_cast<float4*>(out + (size_t)row * ldo + j);
 #pragma unroll
-                            for (int e = 0; e < 32; e += 4)
-                                dst[e / 4] = make_float4((__uint_as_float(acc[e]) + bl[j + e]) * sc,
-                                                         (__uint_as_float(acc[e + 1]) + bl[j + e + 1]) * sc,
-                                                         (__uint_as_float(acc[e + 2]) + bl[j + e + 2]) * sc,
-                                                         (__uint_as_float(acc[e + 3]) + bl[j + e + 3]) * sc);
+                                for (int e = 0; e < 32; e += 4)
+                                    dst[e / 4] = make_float4((__uint_as_float(acc[e]) + bl[j + e]) * sc,
+                                                             (__uint_as_float(acc[e + 1]) + bl[j + e + 1]) * sc,
+                                                             (__uint_as_float(acc[e + 2]) + bl[j + e + 2]) * sc,
+                                                             (__uint_as_float(acc[e + 3]) + bl[j + e + 3]) * sc);
+                            }
                         }
+                        tc_fence_before();
+                        // the next round's encode overwrites this tile's operand
+                        // only after its last MMAs, which acc_full saw complete
                     }
-                    tc_fence_before();
                 }
             }
         }
@@ -251,7 +273,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, kHid);
+        tmem_dealloc(tmem, kTiles * kHid);
     }
 }
 
