@@ -84,6 +84,23 @@ class TidasOperator:
         return tidas_adjoint(self.kernels, y, variant=self.variant, out=out)
 
 
+class TidasBandOperator:
+    """tiDAS with 2D band kernels [nz, kz, taps] (the PSF's axial extent kept)."""
+
+    def __init__(self, kernels, variant=capi.VARIANT_DIRECT):
+        if variant != capi.VARIANT_DIRECT:
+            raise ValueError("the band operator in FISTA runs on FP32 iterates (DIRECT)")
+        self.kernels, self.variant = kernels, variant
+
+    def forward(self, x, out):
+        from .ops import tidas_forward_2d
+        return tidas_forward_2d(self.kernels, x, variant=self.variant, out=out)
+
+    def adjoint(self, y, out):
+        from .ops import tidas_adjoint_2d
+        return tidas_adjoint_2d(self.kernels, y, variant=self.variant, out=out)
+
+
 class ExactOperator:
     def __init__(self, plan: DasPlan, frames=1):
         if plan.rf_dtype != torch.float32:

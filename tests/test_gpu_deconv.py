@@ -87,6 +87,30 @@ def test_fista_tidas_matches_oracle():
     assert F.objective(H, x_o, b32, lam) < F.objective(H, 0 * x_o, b32, lam)
 
 
+def test_fista_band_operator_matches_oracle():
+    # FISTA on the 2D band model (kz x taps kernels) against FP64 FISTA over
+    # the oracle's band convolution
+    import oracle
+    from oracle import fista as F
+    deconv = D()
+    nz, nx, kz, taps = 24, 96, 7, 15
+    kern = generators.standard_normal((nz, kz, taps), (47,), np.float32) * 0.3
+    x_true = generators.bernoulli_normal((1, nz, nx), 0.05, (48,))
+    noise = generators.standard_normal((1, nz, nx), (49,), np.float32)
+    H = lambda v: oracle.tidas_conv2d(kern, v)
+    Ht = lambda v: oracle.tidas_conv2d_adjoint(kern, v)
+    b32 = (H(x_true) + 0.01 * noise).astype(np.float32)
+    v0 = generators.standard_normal(b32.shape, (50,))
+    L, _ = F.power_iteration(H, Ht, v0, 30)
+    op = deconv.TidasBandOperator(to_dev(kern))
+    Lg, _ = deconv.power_iteration(op, to_dev(v0), 30)
+    assert Lg == pytest.approx(L, rel=1e-5)
+    lam = 0.01 * np.abs(Ht(b32)).max()
+    x_o = F.fista(H, Ht, b32.astype(np.float64), lam, 1.01 * L, 60)
+    x_g = host(deconv.fista(op, to_dev(b32), lam, 1.01 * L, 60))
+    assert rel_l2(x_g, x_o) <= 1e-4
+
+
 def test_fista_exact_operator_matches_oracle():
     import oracle
     from oracle import fista as F
