@@ -132,6 +132,32 @@ def active_updates(g):
     return cnt * len(angles_rad(g))
 
 
+# --------------------------------------------------------- multi-rank logic
+# Frames are sharded across ranks with no data-path collective: every rank
+# synthesises its own batch (its own scatterer seeds) and beamforms it; only
+# the step time is reduced (max over ranks), and the value counts the frames of
+# all ranks.
+def rank_seed_base(rank):
+    """Scatterer seed base of a rank's frames: frame f of rank r draws from
+    seed (1 + 1000 r, f), so no two ranks image the same frame."""
+    return 1 + 1000 * rank
+
+
+def max_over_ranks(torch, values, world, device):
+    """Element-wise max of a list of floats over the ranks (one all-reduce)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_mpix_s(frames_per_rank, pixels_per_frame, world, ms):
+    """Weak scaling: every rank's frames, divided by the slowest rank's time."""
+    return frames_per_rank * pixels_per_frame * world / (ms * 1e-3) / 1e6
+
+
 def make_rf(plan, torch, nf, seed_base=1):
     """Synthesise nf frames of channel data on the GPU (speckle + targets)."""
     from tidas_workloads import generators
@@ -196,7 +222,7 @@ def run_ours(args):
     hbm_peak, bf16_peak, peak_src = peaks()
     g = presets.geometry(GEOM)
     P16 = ops.DasPlan(g, rf_dtype=torch.float16)
-    rf = make_rf(P16, torch, BATCH, seed_base=1 + 1000 * rank)
+    rf = make_rf(P16, torch, BATCH, seed_base=rank_seed_base(rank))
     img = torch.empty(P16.img_shape(BATCH), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     npx = g["nx"] * g["nz"]
@@ -209,12 +235,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         ms = time_steps(torch, step, args.steps, args.warmup, stream)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, [ms], world, "cuda")[0]
     clocks = clk.summary()
-    value = BATCH * npx * world / (ms * 1e-3) / 1e6
+    value = whole_job_mpix_s(BATCH, npx, world, ms)
 
     # ---- roofline of the step's dominant kernel, das_tc_kernel.  A step is two
     # launches inside one das_forward call: das_tc_pack_kernel (repacks the
@@ -312,16 +335,13 @@ def run_ours(args):
     gc.enable()
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     ok_e2e = torch.equal(host_out[(n_e2e - 1) & 1], img.cpu())
-    if world > 1:
-        t = torch.tensor([e2e_ms, serial_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms, serial_ms = float(t[0].item()), float(t[1].item())
-    e2e = {"value": BATCH * npx * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mpixels/s",
+    e2e_ms, serial_ms = max_over_ranks(torch, [e2e_ms, serial_ms], world, "cuda")
+    e2e = {"value": whole_job_mpix_s(BATCH, npx, world, e2e_ms), "unit": "Mpixels/s",
            "h2d_bytes_per_step": rf.numel() * 2, "d2h_bytes_per_step": img.numel() * 4,
            "ms_per_step": e2e_ms, "steps": n_e2e,
            "form": "ops.DasStreamer: copies of neighbouring steps overlap the beamforming",
            "image_matches_device_step": bool(ok_e2e),
-           "serial": {"value": BATCH * npx * world / (serial_ms * 1e-3) / 1e6,
+           "serial": {"value": whole_job_mpix_s(BATCH, npx, world, serial_ms),
                       "ms_per_step": serial_ms}}
 
     # ---- tiDAS variants on the 256-frame reflectivity batch
