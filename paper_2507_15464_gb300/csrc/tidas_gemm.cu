@@ -191,29 +191,28 @@ __global__ void __launch_bounds__(gemm::Cfg<RESID>::kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_hi = smem_u32(sA + st * C::kAParts * kChunkBytes);
-                    const uint32_t a_lo = a_hi + kChunkBytes;
-                    int tl[2], cp[2], np = 0;
-                    if ((c & 1) == 0 && c / 2 - 1 >= I.s0) { tl[np] = c / 2 - 1; cp[np] = 2; ++np; }
-                    if (c / 2 < I.s1) { tl[np] = c / 2; cp[np] = c & 1; ++np; }
-                    for (int q = 0; q < np; ++q) {
+                    // descriptors formed once per chunk; a K-step adds 32 bytes (2)
+                    const uint64_t da_hi = desc_sw128_kmajor(smem_u32(sA + st * C::kAParts * kChunkBytes));
+                    const uint64_t da_lo = da_hi + (uint64_t)(kChunkBytes >> 4);
+                    const uint64_t db = desc_sw128_kmajor(smem_u32(bt));
+                    // tile tl (absolute) from Toeplitz part cp of this chunk
+                    auto tile = [&](int tl, int cp) {
                         const uint32_t d = tmem_base + (uint32_t)(ab * kAccCols) +
-                                           (uint32_t)((tl[q] - I.s0) * kN);
-                        const uint32_t bh = smem_u32(bt + cp[q] * kBTileBytes);
-                        const uint32_t bl = bh + 3 * kBTileBytes;
+                                           (uint32_t)((tl - I.s0) * kN);
+                        const uint64_t bh = db + (uint64_t)(cp * (kBTileBytes >> 4));
+                        const uint64_t bl = bh + (uint64_t)(3 * (kBTileBytes >> 4));
 #pragma unroll
                         for (int kk = 0; kk < kKC / 16; ++kk) {
-                            const uint32_t acc = (cp[q] > 0 || kk > 0) ? 1u : 0u;
-                            mma_f16(d, desc_sw128_kmajor(a_hi) + 2 * kk,
-                                    desc_sw128_kmajor(bh) + 2 * kk, kIdesc, acc);
+                            mma_f16(d, da_hi + 2 * kk, bh + 2 * kk, kIdesc,
+                                    (cp > 0 || kk > 0) ? 1u : 0u);
                             if (RESID) {
-                                mma_f16(d, desc_sw128_kmajor(a_lo) + 2 * kk,
-                                        desc_sw128_kmajor(bh) + 2 * kk, kIdesc, 1u);
-                                mma_f16(d, desc_sw128_kmajor(a_hi) + 2 * kk,
-                                        desc_sw128_kmajor(bl) + 2 * kk, kIdesc, 1u);
+                                mma_f16(d, da_lo + 2 * kk, bh + 2 * kk, kIdesc, 1u);
+                                mma_f16(d, da_hi + 2 * kk, bl + 2 * kk, kIdesc, 1u);
                             }
                         }
-                    }
+                    };
+                    if ((c & 1) == 0 && c / 2 - 1 >= I.s0) tile(c / 2 - 1, 2);
+                    if (c / 2 < I.s1) tile(c / 2, c & 1);
                     mma_commit(&empty[st]);
                     if (++st == (uint32_t)C::kStages) { st = 0; ph ^= 1; }
                 }
