@@ -544,6 +544,7 @@ def bench_line(torch, stream):
              "frac_local_below_5pct": float((el_h < 0.05).mean()),
              "frac_global_below_5pct": float((eg_h < 0.05).mean()),
              "theta_p5_p95": [float(np.percentile(th_h, 5)), float(np.percentile(th_h, 95))]}
+        r["fig_3_1"] = line_peaks_and_fwhm(torch, E, rf, g, eps, zf)
         # curves that keep the local error below 5 % for the most scatterers
         good = (el_h < 0.05).sum(axis=1)
         r["best_curve_depth_mm"] = float(E.depth(int(np.argmax(good))) * 1e3)
@@ -574,6 +575,55 @@ def bench_line(torch, stream):
         res[key] = r
         del rf, g
     return res
+
+
+def _fwhm_rows(env, spacing):
+    """Full width at half maximum of each row's main peak, linear
+    interpolation between line points (reporting only)."""
+    out = np.empty(env.shape[0])
+    for k, e in enumerate(env):
+        i = int(np.argmax(e))
+        half = 0.5 * e[i]
+        lo = i
+        while lo > 0 and e[lo - 1] > half:
+            lo -= 1
+        hi = i
+        while hi < e.size - 1 and e[hi + 1] > half:
+            hi += 1
+        left = lo - (e[lo] - half) / (e[lo] - e[lo - 1]) if lo > 0 else float(lo)
+        right = hi + (e[hi] - half) / (e[hi] - e[hi + 1]) if hi < e.size - 1 else float(hi)
+        out[k] = (right - left) * spacing
+    return out
+
+
+def line_peaks_and_fwhm(torch, E, rf, das_lines, eps, z_focus):
+    """Fig. 3.1 / 3.2: for every scatterer, the peak and the FWHM of the DAS
+    line and of its tiDAS reconstruction under the focal point's delay curve
+    (envelopes on the GPU), summarised over depth."""
+    from paper_2507_15464_gb300.ops import envelope
+    D = E.D
+    z = np.array([E.depth(i) for i in range(D)])
+    s_f = int(np.argmin(np.abs(z - z_focus)))
+    ti = E.fixed_lines(rf, s_f, eps)
+    env_d = envelope(das_lines).cpu().numpy().astype(np.float64)
+    env_t = envelope(ti).cpu().numpy().astype(np.float64)
+    dz = (z[-1] - z[0]) / (D - 1)
+    pk_d, pk_t = env_d.max(axis=1), env_t.max(axis=1)
+    fw_d, fw_t = _fwhm_rows(env_d, dz), _fwhm_rows(env_t, dz)
+    near = np.abs(z - z[s_f]) <= 2e-3
+    ratio = pk_t / pk_d
+    dfw = np.abs(fw_t - fw_d)
+    c = E.p["c"]
+    return {"focal_curve_depth_mm": float(z[s_f] * 1e3),
+            "peak_das_over_focal": [float(np.min(pk_d / pk_d[s_f])), float(np.max(pk_d / pk_d[s_f]))],
+            "peak_ratio_tidas_over_das": {"at_focus": float(ratio[s_f]),
+                                          "median_within_2mm": float(np.median(ratio[near])),
+                                          "median_all": float(np.median(ratio))},
+            "fwhm_abs_diff_us": {"at_focus": float(dfw[s_f] * 2 / c * 1e6),
+                                 "median_within_2mm": float(np.median(dfw[near]) * 2 / c * 1e6),
+                                 "median_all": float(np.median(dfw) * 2 / c * 1e6)},
+            "fwhm_das_at_focus_us": float(fw_d[s_f] * 2 / c * 1e6),
+            "note": "FWHM in two-way time of the line's envelope; peaks of the envelopes"}
 
 
 def bench_line_reconstruction(torch, stream, E, rf, theta, eps):

@@ -263,6 +263,12 @@ int tidas_line_das(const tidas_line_params* p, const float* rf, int32_t n_scat, 
 int tidas_line_sweep(const tidas_line_params* p, const float* rf, const float* lines,
                      int32_t r_first, int32_t n_scat, double eps, float* theta,
                      float* err_local, float* err_global, void* stream);
+/* The tiDAS reconstruction of every scatterer under one delay curve s
+ * (Eq. (2.8) with its theta, Eq. (2.12)): out[n_scat][n_depths] (FP32) row
+ * rs = theta a_s for the scatterer on point r_first + rs, with rf, eps and
+ * the window as in tidas_line_sweep (theta = 0 where a_s vanishes). */
+int tidas_line_fixed(const tidas_line_params* p, const float* rf, int32_t r_first, int32_t n_scat,
+                     int32_t s, double eps, float* out, void* stream);
 /* The window half-width of Section 3.2: half the FWHM of the DAS PSF at the
  * focal point.  There the transmit and receive delays align every
  * contribution, so the PSF's time profile is the pulse and

@@ -96,6 +96,7 @@ _SIG = {
     "tidas_line_combine": [ctypes.POINTER(line_params), _P, _I, _P, _P, _P],
     "tidas_line_model": [ctypes.POINTER(line_params), _P, _I, _P, ctypes.c_double, _P, _P],
     "tidas_line_envelope": [_I, _I, _P, _P, _P],
+    "tidas_line_fixed": [ctypes.POINTER(line_params), _P, _I, _I, _I, ctypes.c_double, _P, _P],
 }
 _RESTYPE = {"tidas_band_workspace_bytes": _S}
 EXPORTED = list(_SIG) + ["tidas_last_error"]
@@ -222,6 +223,11 @@ def tidas_line_combine(p, rf, n_scat, amps, rf_line, stream=0):
 
 def tidas_line_model(p, rf_line, s, theta, eps, out, stream=0):
     return _check(load().tidas_line_model(ctypes.byref(p), rf_line, s, theta, eps, out, stream))
+
+
+def tidas_line_fixed(p, rf, r_first, n_scat, s, eps, out, stream=0):
+    return _check(load().tidas_line_fixed(ctypes.byref(p), rf, r_first, n_scat, s, eps, out,
+                                          stream))
 
 
 def tidas_line_envelope(n_rows, n, x, env, stream=0):

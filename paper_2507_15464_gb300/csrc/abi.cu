@@ -19,6 +19,8 @@ int launch_line_combine(const tidas_line_params& p, const float* rf, int n_scat,
 int launch_line_model(const tidas_line_params& p, const float* S, int s, const float* theta,
                       double eps, float* out, cudaStream_t st);
 int launch_line_envelope(int n_rows, int n, const float* x, float* env, cudaStream_t st);
+int launch_line_fixed(const tidas_line_params& p, const float* rf, int r_first, int n_scat, int s,
+                      double eps, float* out, cudaStream_t st);
 int launch_line_synth(const tidas_line_params& p, int r_first, int n_scat, float* rf,
                       cudaStream_t st);
 int launch_line_das(const tidas_line_params& p, const float* rf, int n_scat, float* lines,
@@ -259,4 +261,16 @@ extern "C" int tidas_line_envelope(int32_t n_rows, int32_t n, const float* x, fl
     TIDAS_REQUIRE(n_rows >= 1 && n_rows <= 65535 && n >= 1 && n <= 18000,
                   "tidas_line_envelope: need 1 <= n_rows <= 65535 and 1 <= n <= 18000");
     return launch_line_envelope(n_rows, n, x, env, S_(stream));
+}
+
+extern "C" int tidas_line_fixed(const tidas_line_params* p, const float* rf, int32_t r_first,
+                                int32_t n_scat, int32_t s, double eps, float* out, void* stream) {
+    int rc = validate_line(p);
+    if (rc) return rc;
+    TIDAS_REQUIRE(rf && out, "tidas_line_fixed: null pointer");
+    TIDAS_REQUIRE(n_scat >= 1 && r_first >= 0 && r_first + n_scat <= p->n_depths,
+                  "tidas_line_fixed: scatterers outside the line");
+    TIDAS_REQUIRE(s >= 0 && s < p->n_depths, "tidas_line_fixed: curve outside the line");
+    TIDAS_REQUIRE(eps > 0.0, "tidas_line_fixed: eps must be positive");
+    return launch_line_fixed(*p, rf, r_first, n_scat, s, eps, out, S_(stream));
 }

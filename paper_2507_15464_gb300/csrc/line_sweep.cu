@@ -288,6 +288,40 @@ __device__ void sweep_curve(const line::Dev& L, const LineTab& T, int r, int s, 
     __syncwarp();
 }
 
+// The windows of Eq. (2.8) for scatterer depth zr: per channel the samples k
+// with |k / fs - t_n| <= eps (t_n the echo arrival), tested one by one from
+// just below t_n - eps, then the windowed samples from k_lo - 2 into shared
+// memory (kStage per channel at stride kStride, zero outside the window).
+// Called by the whole block; ends with the staged samples visible to it.
+__device__ void stage_windows(const line::Dev& L, const float* __restrict__ S, double zr,
+                              double eps, float* __restrict__ sw, int* __restrict__ klo,
+                              int* __restrict__ khi) {
+    using namespace line;
+    for (int n = threadIdx.x; n < L.N; n += blockDim.x) {
+        const double t = arrival(L, elem_x(L, n), zr);
+        const long k0 = (long)floor(__dmul_rn(__dsub_rn(t, eps), L.fs)) - 1;
+        const int span = (int)ceil(2.0 * eps * L.fs) + 4;
+        long first = 1, last = 0;
+        for (int j = 0; j <= span; ++j) {
+            const long k = k0 + j;
+            if (k < 0 || k >= L.S) continue;
+            if (fabs(__dsub_rn(__ddiv_rn((double)k, L.fs), t)) <= eps) {
+                if (first > last) first = k;
+                last = k;
+            }
+        }
+        klo[n] = (int)first;  // an empty window has klo > khi
+        khi[n] = (int)last;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < L.N * kStage; q += blockDim.x) {
+        const int n = q / kStage, j = q % kStage;
+        const int k = klo[n] - 2 + j;
+        sw[n * kStride + j] = (k >= klo[n] && k <= khi[n]) ? __ldg(S + (size_t)n * L.S + k) : 0.f;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(32 * line::kSweepWarps) line_sweep_kernel(
     line::Dev L, LineTab T, const float* __restrict__ rf, const float* __restrict__ lines,
     int r_first, int n_scat, double eps, float* __restrict__ theta, float* __restrict__ e_loc,
@@ -308,30 +342,7 @@ __global__ void __launch_bounds__(32 * line::kSweepWarps) line_sweep_kernel(
     const double zr = depth(L, r);
     const float* S = rf + (size_t)rs * N * L.S;
 
-    // window of every channel: the samples k with |k / fs - t_n| <= eps,
-    // tested one by one from just below t_n - eps (at most 2 eps fs + 4)
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const double t = arrival(L, elem_x(L, n), zr);
-        const long k0 = (long)floor(__dmul_rn(__dsub_rn(t, eps), L.fs)) - 1;
-        const int span = (int)ceil(2.0 * eps * L.fs) + 4;
-        long first = 1, last = 0;
-        for (int j = 0; j <= span; ++j) {
-            const long k = k0 + j;
-            if (k < 0 || k >= L.S) continue;
-            if (fabs(__dsub_rn(__ddiv_rn((double)k, L.fs), t)) <= eps) {
-                if (first > last) first = k;
-                last = k;
-            }
-        }
-        klo[n] = (int)first;  // an empty window has klo > khi
-        khi[n] = (int)last;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < N * kStage; q += blockDim.x) {
-        const int n = q / kStage, j = q % kStage;
-        const int k = klo[n] - 2 + j;
-        sw[n * kStride + j] = (k >= klo[n] && k <= khi[n]) ? __ldg(S + (size_t)n * L.S + k) : 0.f;
-    }
+    stage_windows(L, S, zr, eps, sw, klo, khi);
     if (threadIdx.x == 0) {
         s_gg = 0.0;
         // local points: |z_i - z_r| <= c eps / 2
@@ -396,6 +407,54 @@ __global__ void __launch_bounds__(32 * line::kSweepWarps) line_sweep_kernel(
             e_glob[o] = g2f > 0.f ? (th * th * aa - 2.f * th * ag + g2f) / g2f : 0.f;
         }
         __syncwarp();
+    }
+}
+
+// Fixed-curve lines of one delay curve s for every scatterer (Eq. (2.8)),
+// each scaled by its theta (Eq. (2.12)): out[rs][i] = theta a_s[i].  Block per
+// scatterer; warp 0 builds b (its own curve), warp 1 a_s, then warp 0 scales.
+__global__ void __launch_bounds__(64) line_fixed_kernel(line::Dev L, LineTab T,
+                                                        const float* __restrict__ rf, int r_first,
+                                                        int s, double eps,
+                                                        float* __restrict__ out) {
+    using namespace line;
+    extern __shared__ float sm[];
+    const int N = L.N, D = L.D;
+    float* sw = sm;                              // [N][kStride]
+    float* abufs = sw + N * kStride;             // [2][D]: b, a_s
+    int* klo = (int*)(abufs + 2 * D);
+    int* khi = klo + N;
+    __shared__ int s_rng[4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rs = blockIdx.x, r = r_first + rs;
+    stage_windows(L, rf + (size_t)rs * N * L.S, depth(L, r), eps, sw, klo, khi);
+    {
+        int lo, hi;
+        sweep_curve(L, T, r, warp == 0 ? r : s, lane, sw, klo, khi, abufs + warp * D, lo, hi);
+        if (lane == 0) {
+            s_rng[2 * warp] = lo;
+            s_rng[2 * warp + 1] = hi;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int blo = s_rng[0], bhi = s_rng[1], alo = s_rng[2], ahi = s_rng[3];
+        const float* b = abufs;
+        const float* a = abufs + D;
+        float ab = 0.f, aa = 0.f;
+        for (int i = alo + lane; i <= ahi; i += 32) {
+            const float bi = (i >= blo && i <= bhi) ? b[i] : 0.f;
+            ab += a[i] * bi;
+            aa += a[i] * a[i];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            ab += __shfl_xor_sync(0xffffffffu, ab, o);
+            aa += __shfl_xor_sync(0xffffffffu, aa, o);
+        }
+        const float th = aa > 0.f ? ab / aa : 0.f;
+        for (int i = lane; i < D; i += 32)
+            out[(size_t)rs * D + i] = (i >= alo && i <= ahi) ? th * a[i] : 0.f;
     }
 }
 
@@ -640,5 +699,34 @@ int launch_line_envelope(int n_rows, int n, const float* x, float* env, cudaStre
                          (int)smem);
     line_envelope_kernel<<<n_rows, 256, smem, st>>>(n, x, env);
     return check_launch("line_envelope_kernel");
+}
+}  // namespace tidas
+
+namespace tidas {
+int launch_line_fixed(const tidas_line_params& p, const float* rf, int r_first, int n_scat, int s,
+                      double eps, float* out, cudaStream_t st) {
+    const line::Dev L = line_dev(p);
+    if (2.0 * eps * L.fs + 1.0 > line::kStage - 5)
+        return set_error(TIDAS_ERR_UNSUPPORTED,
+                         "line fixed: the window (2 eps fs + 1 samples) must stay below %d",
+                         line::kStage - 5);
+    const size_t smem = sizeof(float) * ((size_t)L.N * line::kStride + 2 * (size_t)L.D) +
+                        sizeof(int) * 2 * (size_t)L.N;
+    if (smem > 220 * 1024)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "line fixed: %d depths x %d elements do not fit",
+                         L.D, L.N);
+    void* ws = nullptr;
+    TIDAS_CUDA(cudaMallocAsync(&ws, table_bytes(L), st));
+    const LineTab T = carve(L, ws);
+    line_table_kernel<<<(L.D * L.N + 255) / 256, 256, 0, st>>>(L, T);
+    int rc = check_launch("line_table_kernel");
+    if (rc == TIDAS_OK) {
+        cudaFuncSetAttribute(line_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        line_fixed_kernel<<<n_scat, 64, smem, st>>>(L, T, rf, r_first, s, eps, out);
+        rc = check_launch("line_fixed_kernel");
+    }
+    cudaFreeAsync(ws, st);
+    return rc;
 }
 }  // namespace tidas

@@ -286,6 +286,16 @@ class LineExperiment:
                               *[_ptr(o) for o in outs], _stream())
         return tuple(outs)
 
+    def fixed_lines(self, rf, s, eps, r_first=0, out=None):
+        """theta a_s for every scatterer under delay curve s: [n_scat, n_depths]."""
+        n = rf.shape[0]
+        _need(rf, torch.float32, (n, self.N, self.S), "rf")
+        out = out if out is not None else torch.empty((n, self.D), dtype=torch.float32,
+                                                      device=rf.device)
+        capi.tidas_line_fixed(self.P, _ptr(rf), r_first, n, int(s), float(eps), _ptr(out),
+                              _stream())
+        return out
+
     def combine(self, rf, amps, out=None):
         """Channel data of a line of scatterers, amps[r] on point r."""
         n = rf.shape[0]

@@ -180,3 +180,22 @@ def test_paper_line_reconstruction_matches_oracle():
     assert rel_l2(das, O.das_line(S_h)) <= 1e-5
     got = host(E.model(S, s, to_dev(np.ascontiguousarray(th[s])), eps))
     assert rel_l2(got, O.model_line(S_h, s, th[s].astype(np.float64), eps)) <= 1e-5
+
+
+def test_fixed_lines_match_oracle():
+    # the tiDAS reconstruction of each scatterer under one delay curve
+    p = small_params()
+    E, O = experiment(p), line_oracle(p)
+    rf = E.synthesize()
+    eps = O.eps()
+    rf_h = host(rf)
+    for s in (20, 9):
+        got = host(E.fixed_lines(rf, s, eps))
+        assert got.shape == (41, 41)
+        for r in (3, 18, 20, 35):
+            S = rf_h[r].astype(np.float64)
+            a = O.fixed_line(S, r, s, eps)
+            th = O.sweep_pair(S, O.das_line(S), r, s, eps)[0]
+            ref = th * a
+            if np.linalg.norm(ref) > 0:
+                assert rel_l2(got[r], ref) <= 1e-4, (r, s)
