@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(256, 2) das_forward_kernel(DasDev d, const RF*
     const int lane = threadIdx.x;
     const int tid = threadIdx.y * 32 + lane;
     const int ix = blockIdx.x * 32 + lane;
-    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    // deepest rows first (widest apertures), so the last blocks are the cheap ones
+    const int iz = (gridDim.y - 1 - blockIdx.y) * blockDim.y + threadIdx.y;
     if (iz >= d.nz) return;  // uniform per warp; no block-wide barrier follows
     const int f0 = blockIdx.z * FB;
     const int A = d.n_angles, NE = d.n_elem, S = d.n_samples, NX = d.nx;

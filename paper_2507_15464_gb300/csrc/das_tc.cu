@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     int16_t* s_tab = (int16_t*)(s_base + A * kM);              // [pair]: window entries
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x;
+    // deepest tiles first: their apertures span the most elements, so the
+    // last wave of CTAs holds the cheap shallow tiles and the tail stays short
+    const int tile = gridDim.x - 1 - blockIdx.x;
     const int tx = tile % tiles_x, tz = tile / tiles_x;
     const int f0 = blockIdx.y * NF;
     const int2 rg = range[tile];
