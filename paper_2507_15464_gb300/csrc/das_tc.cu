@@ -25,18 +25,24 @@
 //  - warps 0, 1: producers of group 0 / group 1: one bulk copy per pair into
 //    the group's ring of K-step chunks (as many pairs in flight as the ring
 //    holds).  Warp 0 also owns tensor memory.
-//  - warps 2-5 / 6-9: the builders of group 0 / group 1.  The groups take
-//    alternate pairs.  Every thread owns one pixel (one row of W_an, one
-//    tensor-memory lane): it erases the 16-byte chunks it wrote two pairs
-//    ago and writes its four weights as swizzled chunks of a 128-byte-swizzled
-//    K-major weight tile (two per group).
+//  - warps 2-5 / 6-9: the builders of group 0 / group 1.  The pairs of a
+//    tile are cut into rounds of one or two consecutive pairs whose K-steps
+//    fit one 64-column weight tile together (at plan creation, greedily from
+//    the first pair), and the groups take alternate rounds.  Every thread
+//    owns one pixel (one row of W_an, one tensor-memory lane): it erases the
+//    16-byte chunks it wrote two rounds ago and writes each pair's four
+//    weights as swizzled chunks of a 128-byte-swizzled K-major weight tile
+//    (two per group), the second pair's columns after the first's.
 //  - warps 10, 11: the MMA warps of group 0 / group 1.  Builders and MMA warp
-//    meet at a named barrier once per pair; then the MMA warp issues that
-//    pair's K-steps into the group's own accumulator while the builders write
-//    the next pair, and one tcgen05.commit per pair frees both the weight tile
-//    and the pair's chunks.  A single thread issues one tcgen05.mma about
+//    meet at a named barrier once per round; then the MMA warp issues the
+//    round's K-steps into the group's own accumulator while the builders write
+//    the next round, and one tcgen05.commit per round frees both the weight
+//    tile and the round's chunks.  A single thread issues one tcgen05.mma about
 //    every 100 cycles, while a 128 x 64 x 16 step occupies the tensor pipe
 //    for about 50, so two issuing threads per CTA (four per SM) keep it fed.
+//    Merging pairs into rounds (0.63 rounds per pair on the 128-element,
+//    11-angle grid) saves a barrier, a commit and the loop bookkeeping of
+//    every merged pair.
 // The epilogue sums the two accumulators.
 #include <climits>
 #include <mutex>
@@ -69,7 +75,12 @@ constexpr int kPackS = 64;                // samples per pack block
 constexpr int kGroups = 2;                // builder groups, one accumulator each
 constexpr int kWTiles = 2 * kGroups;      // weight tiles: two per group
 constexpr int kWBytes = kM * kKW * 2;     // 16 KB
-constexpr int kPairSlots = 8;             // pairs of a group in flight (barrier slots)
+constexpr int kPairSlots = 8;             // rounds of a group in flight (barrier slots)
+// Window entry, 16 bits: 2 * k0 + (8 if the pair is the second of its round)
+// + K-steps (0..4); k0 is a multiple of 8 in [-kMaxK0, kMaxK0].
+constexpr int kMaxK0 = 16376;
+constexpr int kSecond = 8;
+__host__ __device__ constexpr int entry_k0(int e) { return (e >> 4) * 8; }
 constexpr int kMinChunks = 6, kMaxChunks = 32;  // chunks per group ring
 // per group: one producer warp, four builder warps, one MMA warp
 constexpr int kBuilderWarp0 = kGroups;            // warps [0, kGroups): producers
@@ -82,10 +93,10 @@ constexpr size_t kSmemTwoPerSM = 115712;  // (228 KB - 2 x 1 KB reserved) / 2
 constexpr size_t kSmemMax = 227 * 1024;
 // one K-step chunk = 16 sample rows of NF frames
 __host__ __device__ constexpr int chunk_bytes(int NF) { return kKC * NF * 2; }
-// align | weight tiles | chunk rings | barriers, flags (1 KB) | prev [kWTiles][kM] int8 |
+// align | weight tiles | chunk rings | barriers, flags (1 KB) |
 // transmit split [A][kM] int2 | window entries [A * NE] int16
 __host__ __device__ constexpr size_t fixed_bytes(int A, int NE) {
-    return 1024 + (size_t)kWTiles * kWBytes + 1024 + (size_t)kWTiles * kM + (size_t)A * kM * 8 +
+    return 1024 + (size_t)kWTiles * kWBytes + 1024 + (size_t)A * kM * 8 +
            (((size_t)A * NE * 2 + 15) & ~(size_t)15);
 }
 __host__ __device__ constexpr size_t smem_bytes(int NF, int C, int A, int NE) {
@@ -179,10 +190,24 @@ __device__ __forceinline__ bool group_bar(int grp, int stop) {
     return grp == 0 ? named_bar_or<2>(kCount, stop) : named_bar_or<3>(kCount, stop);
 }
 
-// Per-(tile, angle, element) window: entry = k0 + ksteps, k0 a multiple of 8
-// and ksteps in 0..4 (0: no contributing pixel, or a window wholly outside
-// the record, whose samples are all zero).  Per tile: the range of
-// contributing elements.
+// Pairs in the round that starts at pair q: two when pair q + 1 is marked as
+// the second of its round.
+__device__ __forceinline__ int round_len(const int16_t* s_tab, int q, int npairs) {
+    return (q + 1 < npairs && (s_tab[q + 1] & dtc::kSecond)) ? 2 : 1;
+}
+
+// First pair of group grp's next round after the one at q (rounds alternate
+// between the groups); npairs or more when there is none.
+__device__ __forceinline__ int next_round(const int16_t* s_tab, int q, int npairs) {
+    int q2 = q + round_len(s_tab, q, npairs);
+    if (q2 < npairs) q2 += round_len(s_tab, q2, npairs);
+    return q2;
+}
+
+// Per-(tile, angle, element) window: entry = 2 k0 + ksteps, k0 a multiple of
+// 8 and ksteps in 0..4 (0: no contributing pixel, or a window wholly outside
+// the record, whose samples are all zero; k0 is then 0).  Per tile: the range
+// of contributing elements.
 __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __restrict__ tab,
                                     int2* __restrict__ range, int* __restrict__ bad) {
     const int NE = d.n_elem, A = d.n_angles;
@@ -209,16 +234,20 @@ __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __res
         if (lo <= hi) {
             // taps i-1 .. i+2 (cubic) or i .. i+1 (linear), one sample of slack each side
             const int c_lo = lo - 2, c_hi = hi + 3;
-            const int k0 = (int)floorf((float)c_lo / 8.f) * 8;
+            int k0 = (int)floorf((float)c_lo / 8.f) * 8;
             const int span = c_hi - k0 + 1;
             int steps = (span + dtc::kKC - 1) / dtc::kKC;
-            // the kernel keeps a 16-bit copy of the entry in shared memory
-            if (steps > dtc::kMaxSteps || k0 < -32760 || k0 > 32760) atomicExch(bad, 1);
+            if (steps > dtc::kMaxSteps) atomicExch(bad, 1);
             steps = min(steps, dtc::kMaxSteps);
             // a window that misses [0, n_samples) reads only zeros; any other
             // one lies inside the packed record's zero margins
-            if (k0 + dtc::kKC * steps <= 0 || k0 >= d.n_samples) steps = 0;
-            entry = k0 + steps;
+            if (k0 + dtc::kKC * steps <= 0 || k0 >= d.n_samples) {
+                steps = 0;
+                k0 = 0;
+            }
+            // the kernel keeps a 16-bit copy of the entry in shared memory
+            if (k0 < -dtc::kMaxK0 || k0 > dtc::kMaxK0) atomicExch(bad, 1);
+            entry = 2 * k0 + steps;
             atomicMin(&range[tile].x, n);
             atomicMax(&range[tile].y, n);
         }
@@ -246,8 +275,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     uint32_t* tmem_slot = (uint32_t*)(done + kGroups);
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
     int* s_used = (int*)(tmem_slot + 2);                       // [kGroups]
-    int8_t* prev = (int8_t*)((uint8_t*)full + 1024);           // [kWTiles][kM] (unused slot)
-    int2* s_base = (int2*)(prev + kWTiles * kM);               // [A][kM]: transmit split
+    int2* s_base = (int2*)((uint8_t*)full + 1024);             // [A][kM]: transmit split
     int16_t* s_tab = (int16_t*)(s_base + A * kM);              // [pair]: window entries
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -312,13 +340,16 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             uint8_t* ring = sC + grp * C * CB;
             const __half* src_tile = packed + (size_t)blockIdx.y * A * NE * Sp * NF;
             int head = 0, free_chunks = C, oldest = 0, j = 0;
-            int n = n_lo + grp / A, a = grp % A;
+            int qa = 0, n = n_lo, a = 0;  // pair qa is (element n, angle a)
+            uint32_t pend = 0;            // K-steps of the rounds in flight, 3 bits per slot
             bool bad = false;
-            for (int q = grp; q < npairs && !bad; q += kGroups, ++j) {
-                const int e = s_tab[q];
-                const int steps = e & 7;
-                // reuse of the pair slot, and room for this pair's chunks:
-                // retire the oldest pairs in flight
+            int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
+            for (; q < npairs && !bad; q = next_round(s_tab, q, npairs), ++j) {
+                const int len = round_len(s_tab, q, npairs);
+                const int e0 = s_tab[q], e1 = len == 2 ? s_tab[q + 1] : 0;
+                const int steps = (e0 & 7) + (e1 & 7);
+                // reuse of the round slot, and room for this round's chunks:
+                // retire the oldest rounds in flight
                 while (!bad && oldest < j && (oldest <= j - kPairSlots || free_chunks < steps)) {
                     if (!mbar_wait_or_abort(&gempty[oldest % kPairSlots],
                                             (uint32_t)(oldest / kPairSlots) & 1u, s_abort,
@@ -326,30 +357,37 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                         bad = true;
                         break;
                     }
-                    free_chunks += s_tab[grp + kGroups * oldest] & 7;
+                    free_chunks += (int)(pend >> (3 * (oldest % kPairSlots))) & 7;
                     ++oldest;
                 }
                 if (bad) break;
+                const int sh = 3 * (j % kPairSlots);
+                pend = (pend & ~(7u << sh)) | ((uint32_t)steps << sh);
                 uint64_t* bar = &gfull[j % kPairSlots];
                 mbar_arrive_expect_tx(bar, (uint32_t)(steps * CB));
-                if (steps) {
-                    // sample rows k0 .. k0 + 16 steps of row (a, n): contiguous
-                    const uint8_t* src = reinterpret_cast<const uint8_t*>(
-                        src_tile + ((size_t)(a * NE + n) * Sp + (size_t)((e & ~7) + kPad)) * NF);
-                    const int first = steps <= C - head ? steps : C - head;
-                    bulk_load(ring + head * CB, src, (uint32_t)(first * CB), bar);
-                    if (first < steps)
-                        bulk_load(ring, src + (size_t)first * CB, (uint32_t)((steps - first) * CB),
-                                  bar);
+                for (int p = 0; p < len; ++p) {
+                    a += q + p - qa;
+                    qa = q + p;
+                    while (a >= A) {
+                        a -= A;
+                        ++n;
+                    }
+                    const int e = p ? e1 : e0;
+                    const int sp = e & 7;
+                    if (sp) {
+                        // sample rows k0 .. k0 + 16 sp of row (a, n): contiguous
+                        const uint8_t* src = reinterpret_cast<const uint8_t*>(
+                            src_tile + ((size_t)(a * NE + n) * Sp + (size_t)(entry_k0(e) + kPad)) * NF);
+                        const int first = sp <= C - head ? sp : C - head;
+                        bulk_load(ring + head * CB, src, (uint32_t)(first * CB), bar);
+                        if (first < sp)
+                            bulk_load(ring, src + (size_t)first * CB, (uint32_t)((sp - first) * CB),
+                                      bar);
+                    }
+                    head += sp;
+                    if (head >= C) head -= C;
                 }
-                head += steps;
-                if (head >= C) head -= C;
                 free_chunks -= steps;
-                a += kGroups;
-                while (a >= A) {
-                    a -= A;
-                    ++n;
-                }
             }
             if (*s_abort) {
                 // the consumers gave up: let the copies still in flight land
@@ -370,26 +408,28 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         uint64_t* gfull = full + grp * kPairSlots;
         uint64_t* gempty = empty + grp * kPairSlots;
         const uint32_t ring = smem_u32(sC + grp * C * CB);
-        int pos = 0, j = 0;  // first chunk of pair j in the ring
+        int pos = 0, j = 0;  // first chunk of round j in the ring
         bool first = true, bad = false;
-        for (int q = grp; q < npairs; q += kGroups, ++j) {
-            // Pair j - 1's MMAs must be complete before this barrier: past it the
-            // builders write pair j + 1 into the tile pair j - 1 read.  (Its MMAs
-            // ran while the builders wrote pair j, so this rarely waits.)
+        int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
+        for (; q < npairs; q = next_round(s_tab, q, npairs), ++j) {
+            // Round j - 1's MMAs must be complete before this barrier: past it the
+            // builders write round j + 1 into the tile round j - 1 read.  (Its MMAs
+            // ran while the builders wrote round j, so this rarely waits.)
             if (lane == 0 && j >= 1 && !bad)
                 bad = !mbar_wait_or_abort(&gempty[(j - 1) % kPairSlots],
                                           (uint32_t)((j - 1) / kPairSlots) & 1u, s_abort,
                                           &g_das_tc_wait_error, 304);
-            // the group's weight tile of pair q is written (leave together on an abort)
+            // the group's weight tile of round j is written (leave together on an abort)
             if (group_bar(grp, bad || *s_abort)) break;
-            const int steps = s_tab[q] & 7;
+            const int steps =
+                (s_tab[q] & 7) + (round_len(s_tab, q, npairs) == 2 ? s_tab[q + 1] & 7 : 0);
             if (lane == 0) {
                 if (!bad && mbar_wait_or_abort(&gfull[j % kPairSlots],
                                                (uint32_t)(j / kPairSlots) & 1u, s_abort,
                                                &g_das_tc_wait_error, 303)) {
                     tc_fence_after();
                     const uint64_t wdesc =
-                        desc_sw128_kmajor(smem_u32(sW + (q & (kWTiles - 1)) * kWBytes));
+                        desc_sw128_kmajor(smem_u32(sW + (grp + kGroups * (j & 1)) * kWBytes));
                     for (int kk = 0; kk < steps; ++kk) {
                         int c = pos + kk;
                         if (c >= C) c -= C;
@@ -414,7 +454,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         named_bar_arrive<1>(kEpiBarCount);
     } else {
         // ------------------- weight tiles, one pixel per thread; group g takes
-        // pairs g, g + 2, ... into weight tiles g and g + 2
+        // rounds g, g + 2, ... into weight tiles g and g + 2
         const int grp = (warp - kBuilderWarp0) >> 2;
         const int m = 32 * (warp & 3) + lane;  // tensor-memory lane = pixel row of W
         const int ix = tx * kTX + m % kTX, iz = tz * kTZ + m / kTX;
@@ -424,86 +464,111 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
         const int swz = m & 7;
         float w = 0.f, exc = 0.f;
-        int prev_a = -1, prev_b = -1;
-        int cur_n = -1;
-        int n = n_lo + grp / A, a = grp % A;
-        // lateral offset of the group's next element, loaded one element ahead
-        // (a single-angle plan gives each group every other element)
-        int pre_n = n;
-        float dxs_next = n <= n_hi ? __ldg(d.dxs + (size_t)n * d.nx + ixc) : 0.f;
-        bool bad = false;
+        // columns this thread last wrote into the group's two tiles, one byte
+        // per pair of the round that wrote them (0xff: none); tile j & 1 in
+        // bits 16 (j & 1) .. 16 (j & 1) + 15
+        uint32_t prev = 0xffffffffu;
+        int n = n_lo, a = 0;  // at the top of a round: its first pair is (element n, angle a)
+        // apodization and receive excess of element n; the lateral offset of
+        // element n + 1 is loaded one element ahead
+        float dxs_next = 0.f;
+        if (npairs > 0) {
+            const float dxs = __ldg(d.dxs + (size_t)n * d.nx + ixc);
+            w = valid ? apod_weight(dxs, zs, d.fnum) : 0.f;
+            exc = rx_excess(dxs, zs);
+            if (n + 1 <= n_hi) dxs_next = __ldg(d.dxs + (size_t)(n + 1) * d.nx + ixc);
+        }
         int j = 0;
-        for (int q = grp; q < npairs; q += kGroups, ++j) {
-            if (n != cur_n) {
-                cur_n = n;
-                const float dxs = n == pre_n ? dxs_next : __ldg(d.dxs + (size_t)n * d.nx + ixc);
-                pre_n = n + (A == 1 ? kGroups : 1);
-                if (pre_n <= n_hi) dxs_next = __ldg(d.dxs + (size_t)pre_n * d.nx + ixc);
-                w = valid ? apod_weight(dxs, zs, d.fnum) : 0.f;
-                exc = rx_excess(dxs, zs);
-            }
-            const int st = q & (kWTiles - 1);
-            const int e = s_tab[q];
-            const int k0 = e & ~7, steps = e & 7;
-            // the tile was last read by this group's pair j - 2, whose MMAs the
+        int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
+        a = q;
+        for (; q < npairs; ++j) {
+            const int len = round_len(s_tab, q, npairs);
+            // the tile was last read by this group's round j - 2, whose MMAs the
             // MMA warp saw complete before the previous group barrier
-            if (!bad) {
-                uint8_t* W = rowp + st * kWBytes;
-                // column of the chunk this thread last wrote into this tile (-1: none);
-                // the group's two tiles alternate with j
-                const int pc = (j & 1) ? prev_b : prev_a;
-                if (pc >= 0) {
-                    *reinterpret_cast<uint4*>(W + (((pc >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
-                    if ((pc & 7) > 4)
-                        *reinterpret_cast<uint4*>(W + ((((pc >> 3) + 1) ^ swz) << 4)) =
+            {
+                uint8_t* W = rowp + (grp + kGroups * (j & 1)) * kWBytes;
+                const int shj = 16 * (j & 1);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int pc = (int)(int8_t)(prev >> (shj + 8 * p));
+                    if (pc >= 0) {
+                        *reinterpret_cast<uint4*>(W + (((pc >> 3) ^ swz) << 4)) =
                             make_uint4(0, 0, 0, 0);
-                }
-                int nc = -1;
-                if (w != 0.f) {
-                    const int2 bs = s_base[a * kM + m];
-                    const float uf = __int_as_float(bs.y) + exc;
-                    const float fl = floorf(uf);
-                    const float phi = uf - fl;
-                    const int i = bs.x + (int)fl;
-                    float v[4];
-                    int c;
-                    if (d.interp == TIDAS_INTERP_CUBIC) {
-                        keys_weights(phi, v[0], v[1], v[2], v[3]);
-                        c = i - 1 - k0;
-                    } else {
-                        v[0] = 1.f - phi;
-                        v[1] = phi;
-                        v[2] = 0.f;
-                        v[3] = 0.f;
-                        c = i - k0;
-                    }
-                    // inside the window by the table's construction, unless the
-                    // window misses the record (steps 0)
-                    if (c >= 0 && c + 3 < steps * kKC) {
-                        const __half2 h01 = __floats2half2_rn(w * v[0], w * v[1]);
-                        const __half2 h23 = __floats2half2_rn(w * v[2], w * v[3]);
-                        const uint64_t pk = (uint64_t)*reinterpret_cast<const uint32_t*>(&h01) |
-                                            ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
-                        uint4 lo, hi;
-                        place4(pk, c & 7, lo, hi);
-                        *reinterpret_cast<uint4*>(W + (((c >> 3) ^ swz) << 4)) = lo;
-                        if ((c & 7) > 4)
-                            *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
-                        nc = c;
+                        if ((pc & 7) > 4)
+                            *reinterpret_cast<uint4*>(W + ((((pc >> 3) + 1) ^ swz) << 4)) =
+                                make_uint4(0, 0, 0, 0);
                     }
                 }
-                if (j & 1)
-                    prev_b = nc;
-                else
-                    prev_a = nc;
+                int nc0 = -1, nc1 = -1;
+                int col0 = 0;  // first column of the pair in the weight tile
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    if (p == 1 && len == 1) break;
+                    a += p;
+                    if (a >= A) {
+                        int dn = 0;
+                        do {
+                            a -= A;
+                            ++n;
+                            ++dn;
+                        } while (a >= A);
+                        const float dxs =
+                            dn == 1 ? dxs_next : __ldg(d.dxs + (size_t)n * d.nx + ixc);
+                        if (n + 1 <= n_hi) dxs_next = __ldg(d.dxs + (size_t)(n + 1) * d.nx + ixc);
+                        w = valid ? apod_weight(dxs, zs, d.fnum) : 0.f;
+                        exc = rx_excess(dxs, zs);
+                    }
+                    const int e = s_tab[q + p];
+                    const int k0 = entry_k0(e), steps = e & 7;
+                    if (w != 0.f) {
+                        const int2 bs = s_base[a * kM + m];
+                        const float uf = __int_as_float(bs.y) + exc;
+                        const float fl = floorf(uf);
+                        const float phi = uf - fl;
+                        const int i = bs.x + (int)fl;
+                        float v[4];
+                        int c;
+                        if (d.interp == TIDAS_INTERP_CUBIC) {
+                            keys_weights(phi, v[0], v[1], v[2], v[3]);
+                            c = i - 1 - k0;
+                        } else {
+                            v[0] = 1.f - phi;
+                            v[1] = phi;
+                            v[2] = 0.f;
+                            v[3] = 0.f;
+                            c = i - k0;
+                        }
+                        // inside the pair's window by the table's construction,
+                        // unless the window misses the record (steps 0)
+                        if (c >= 0 && c + 3 < steps * kKC) {
+                            const __half2 h01 = __floats2half2_rn(w * v[0], w * v[1]);
+                            const __half2 h23 = __floats2half2_rn(w * v[2], w * v[3]);
+                            const uint64_t pk =
+                                (uint64_t)*reinterpret_cast<const uint32_t*>(&h01) |
+                                ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
+                            c += col0;
+                            uint4 lo, hi;
+                            place4(pk, c & 7, lo, hi);
+                            *reinterpret_cast<uint4*>(W + (((c >> 3) ^ swz) << 4)) = lo;
+                            if ((c & 7) > 4)
+                                *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
+                            if (p)
+                                nc1 = c;
+                            else
+                                nc0 = c;
+                        }
+                    }
+                    col0 += steps * kKC;
+                }
+                prev = (prev & ~(0xffffu << shj)) |
+                       ((uint32_t)((nc0 & 0xff) | ((nc1 & 0xff) << 8)) << shj);
             }
             fence_proxy_async_smem();
-            if (group_bar(grp, bad || *s_abort)) break;
-            a += kGroups;
-            while (a >= A) {
-                a -= A;
-                ++n;
-            }
+            if (group_bar(grp, *s_abort)) break;
+            // (n, a) of the first pair of the group's next round
+            const int q2 = next_round(s_tab, q, npairs);
+            a += q2 - (q + len - 1);
+            q = q2;
         }
         named_bar_sync<1>(kEpiBarCount);  // the MMA warps have committed `done`
         // --------------------------------------------------- epilogue: group g
@@ -545,6 +610,41 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     }
 }
 
+// Cut each tile's pairs (element-major, angle-minor, from its first
+// contributing element) into rounds, greedily from the first pair: a pair
+// joins the round of the pair before it when that round holds one pair and
+// their K-steps fit one weight tile.  The second pair of a round is marked in
+// its entry.  One thread per tile.
+__global__ void das_tc_round_kernel(int A, int NE, int tiles, int* __restrict__ tab,
+                                    const int2* __restrict__ range) {
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= tiles) return;
+    const int2 rg = range[tile];
+    if (rg.y < rg.x) return;
+    const int npairs = (rg.y - rg.x + 1) * A;
+    int* tt = tab + (size_t)tile * A * NE + rg.x;
+    int q = 0, n = 0, a = 0;  // pair q is (element rg.x + n, angle a)
+    int e = tt[0];
+    while (q < npairs) {
+        const int q1 = q + 1, a1 = a + 1 < A ? a + 1 : 0, n1 = a + 1 < A ? n : n + 1;
+        if (q1 >= npairs) break;
+        const int e1 = tt[a1 * NE + n1];
+        if ((e & 7) + (e1 & 7) <= dtc::kMaxSteps) {
+            tt[a1 * NE + n1] = e1 | dtc::kSecond;
+            // the round is full: the next one starts at pair q + 2
+            q = q1 + 1;
+            a = a1 + 1 < A ? a1 + 1 : 0;
+            n = a1 + 1 < A ? n1 : n1 + 1;
+            if (q < npairs) e = tt[a * NE + n];
+        } else {
+            q = q1;
+            a = a1;
+            n = n1;
+            e = e1;
+        }
+    }
+}
+
 // Build the window table of an FP16 plan (once, at plan creation).
 int das_tc_prepare(Plan& P) {
     const DasDev& d = P.dev;
@@ -564,6 +664,10 @@ int das_tc_prepare(Plan& P) {
     das_tc_table_kernel<<<(int)(blocks > 152 * 64 ? 152 * 64 : blocks), 256>>>(
         d, P.tc_tiles_x, P.tc_tiles, P.tc_tab, P.tc_range, d_bad);
     int rc = check_launch("das_tc_table_kernel");
+    if (rc) return rc;
+    das_tc_round_kernel<<<(P.tc_tiles + 127) / 128, 128>>>(d.n_angles, d.n_elem, P.tc_tiles,
+                                                          P.tc_tab, P.tc_range);
+    rc = check_launch("das_tc_round_kernel");
     if (rc) return rc;
     int bad = 0;
     TIDAS_CUDA(cudaMemcpy(&bad, d_bad, 4, cudaMemcpyDeviceToHost));
