@@ -119,39 +119,52 @@ __host__ __device__ __forceinline__ int mn_swizzle(int c, int k, int NF) {
 // [nf][R][S] FP16 -> [FT][R][Sp][NF] FP16, sample s at s + kPad, frames past
 // nf and samples outside [0, S) zero, chunks swizzled (mn_swizzle).  One
 // block per (frame tile, row, 64 samples); S is a multiple of 8.
+//
+// The transpose goes through shared memory as 32-bit words, each holding one
+// sample of two neighbouring frames.  Sample row r keeps its NF / 8 chunks of
+// 16 bytes with the chunk index XORed with (r / 8) mod (NF / 8): at NF = 64
+// the word stores of a warp (8 sample rows x 4 frame pairs) and the chunk
+// loads that follow both touch every bank once per wavefront.
 __global__ void __launch_bounds__(256) das_tc_pack_kernel(const __half* __restrict__ rf,
                                                           __half* __restrict__ out, int nf, int R,
                                                           int S, int Sp, int NF) {
     using namespace dtc;
-    __shared__ uint16_t tile[kPackS][64 + 2];
+    __shared__ uint4 tile[kPackS * 8];  // [kPackS rows][NF / 8 chunks]
+    const int cpr = NF / 8;             // chunks per sample row (2, 4 or 8)
     const int nsb = Sp / kPackS;
     const int sb = blockIdx.x % nsb;
     const int row = (blockIdx.x / nsb) % R;
     const int ft = blockIdx.x / (nsb * R);
     const int s0 = sb * kPackS - kPad;
-    // load NF frames x 64 samples as 16-byte chunks of 8 samples
-    for (int i = threadIdx.x; i < NF * (kPackS / 8); i += blockDim.x) {
-        const int f = i / (kPackS / 8), c = i % (kPackS / 8);
-        const int s = s0 + 8 * c, frame = ft * NF + f;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (frame < nf && s >= 0 && s < S)
-            v = __ldg(reinterpret_cast<const uint4*>(rf + ((size_t)frame * R + row) * S + s));
-        const uint16_t* h = reinterpret_cast<const uint16_t*>(&v);
+    uint32_t* t32 = reinterpret_cast<uint32_t*>(tile);
+    // load frame pairs x 64 samples as 16-byte chunks of 8 samples
+    for (int i = threadIdx.x; i < (NF / 2) * (kPackS / 8); i += blockDim.x) {
+        const int c = i % (kPackS / 8), fp = i / (kPackS / 8);
+        const int s = s0 + 8 * c, fa = ft * NF + 2 * fp;
+        uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+        if (s >= 0 && s < S) {
+            if (fa < nf)
+                va = __ldg(reinterpret_cast<const uint4*>(rf + ((size_t)fa * R + row) * S + s));
+            if (fa + 1 < nf)
+                vb = __ldg(
+                    reinterpret_cast<const uint4*>(rf + ((size_t)(fa + 1) * R + row) * S + s));
+        }
+        const uint32_t a[4] = {va.x, va.y, va.z, va.w}, b[4] = {vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
-        for (int t = 0; t < 8; ++t) tile[8 * c + t][f] = h[t];
+        for (int t = 0; t < 4; ++t) {
+            const int r0 = 8 * c + 2 * t;  // rows r0, r0 + 1 share r / 8
+            const int w = 4 * cpr * r0 + 4 * ((fp >> 2) ^ ((r0 >> 3) & (cpr - 1))) + (fp & 3);
+            t32[w] = __byte_perm(a[t], b[t], 0x5410);            // sample r0: frames fa, fa + 1
+            t32[w + 4 * cpr] = __byte_perm(a[t], b[t], 0x7632);  // sample r0 + 1
+        }
     }
     __syncthreads();
     // store 64 sample rows of NF frames, 16-byte chunks swizzled
-    const int cpr = NF / 8;  // chunks per sample row
     __half* dst = out + (((size_t)ft * R + row) * Sp + (size_t)sb * kPackS) * NF;
     for (int i = threadIdx.x; i < kPackS * cpr; i += blockDim.x) {
         const int k = i / cpr, c = i % cpr;
-        uint32_t w[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-            w[t] = (uint32_t)tile[k][8 * c + 2 * t] | ((uint32_t)tile[k][8 * c + 2 * t + 1] << 16);
         *reinterpret_cast<uint4*>(dst + (size_t)k * NF + 8 * mn_swizzle(c, k, NF)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+            tile[k * cpr + (c ^ ((k >> 3) & (cpr - 1)))];
     }
 }
 
