@@ -153,10 +153,12 @@ def test_das_full_batch_fp16_sampled_frames():
 @pytest.mark.parametrize("name,nf,over", [
     ("pw128_compound", 16, {}), ("pw128_compound", 20, {}),
     ("pw64_single", 16, {}), ("pw64_single", 17, dict(nx=100, nz=77, n_samples=1104)),
-    ("pw64_single", 33, dict(interp=1, nx=64, nz=40, z0=6e-3))])
+    ("pw64_single", 33, dict(interp=1, nx=64, nz=40, z0=6e-3)),
+    ("pw128_compound", 64, dict(angles_deg=[-8.0, 0.0, 8.0], nx=80, nz=61, n_samples=2048))])
 def test_das_tensor_core_path(name, nf, over):
-    # ragged pixel tiles, ragged frame tiles, out-of-record windows (TMA zero
-    # fill), linear and cubic interpolation
+    # ragged pixel tiles, ragged frame tiles, out-of-record windows (zero
+    # margins), linear and cubic interpolation; one, three and eleven angles,
+    # so that a round of two pairs spans one or several elements
     g = presets.geometry(name, **over)
     P16, O = plan(g, torch.float16), oracle(g)
     S = g["n_samples"]
