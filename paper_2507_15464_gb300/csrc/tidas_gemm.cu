@@ -511,26 +511,24 @@ size_t band_pack_bytes(int nz, int nx, int nf) {
     return (size_t)nz * ((nf + gemm::kM - 1) / gemm::kM) * gemm2::n_chunks(nx) * gemm::kChunkBytes;
 }
 
-// in [nf][nz][nx] BF16 -> packed [nz][nm][nq] chunk images; one thread per
-// 16-byte piece (8 columns of one frame)
-__global__ void tidas_band_pack_kernel(const __nv_bfloat16* __restrict__ in,
-                                       uint8_t* __restrict__ packed, int nz, int nx, int nf,
-                                       int nm, int nq) {
-    const size_t total = (size_t)nz * nm * nq * gemm::kM * 8;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(i & 7);
-        const int f = (int)((i >> 3) % gemm::kM);
-        const size_t t = (i >> 3) / gemm::kM;  // (z * nm + m) * nq + q
-        const int q = (int)(t % nq);
-        const int m = (int)((t / nq) % nm);
-        const int z = (int)(t / ((size_t)nq * nm));
+// in [nf][nz][nx] BF16 -> packed [nz][nm][nq] chunk images.  One block per
+// chunk image (row z, frame tile m, chunk q); each thread moves 16-byte pieces
+// (8 columns of one frame), 8 consecutive threads one 128-byte frame row.
+__global__ void __launch_bounds__(256) tidas_band_pack_kernel(const __nv_bfloat16* __restrict__ in,
+                                                              uint8_t* __restrict__ packed, int nz,
+                                                              int nx, int nf, int nm, int nq) {
+    const int q = blockIdx.x % nq;
+    const int zm = blockIdx.x / nq;  // z * nm + m
+    const int m = zm % nm, z = zm / nm;
+    uint8_t* const dst = packed + (size_t)blockIdx.x * gemm::kChunkBytes;
+    for (int u = threadIdx.x; u < gemm::kM * 8; u += blockDim.x) {
+        const int j = u & 7, f = u >> 3;
         const int x0 = gemm::kKC * q - 32 + 8 * j;
         const int fr = m * gemm::kM + f;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (fr < nf && x0 >= 0 && x0 < nx)
             v = __ldg(reinterpret_cast<const uint4*>(in + ((size_t)fr * nz + z) * nx + x0));
-        *reinterpret_cast<uint4*>(packed + t * gemm::kChunkBytes + sw128_offset(f, 8 * j)) = v;
+        *reinterpret_cast<uint4*>(dst + sw128_offset(f, 8 * j)) = v;
     }
 }
 
@@ -855,10 +853,11 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
         TIDAS_CUDA(cudaMallocAsync((void**)&packed, need, st));
     }
     const int nm = (nf + gemm::kM - 1) / gemm::kM, nq = gemm2::n_chunks(nx);
-    const size_t pieces = (size_t)nz * nm * nq * gemm::kM * 8;
-    const int pgrid = (int)std::min<size_t>((pieces + 255) / 256, (size_t)sm_count() * 16);
-    tidas_band_pack_kernel<<<pgrid, 256, 0, st>>>((const __nv_bfloat16*)in, packed, nz, nx, nf,
-                                                  nm, nq);
+    const size_t images = (size_t)nz * nm * nq;
+    if (images > (size_t)INT_MAX)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "tidas 2D GEMM: %zu chunk images", images);
+    tidas_band_pack_kernel<<<(unsigned)images, 256, 0, st>>>((const __nv_bfloat16*)in, packed, nz,
+                                                             nx, nf, nm, nq);
     rc = check_launch("tidas_band_pack_kernel");
     if (rc == TIDAS_OK) {
         const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
