@@ -4,6 +4,7 @@ python -m paper_2507_15464_gb300.profile_case das --frames 8 --dtype f16 --iters
 python -m paper_2507_15464_gb300.profile_case tidas --variant 1 --frames 64 --iters 3
 python -m paper_2507_15464_gb300.profile_case tidas2d --variant 1 --kz 16 --frames 256 --iters 3
 python -m paper_2507_15464_gb300.profile_case line --iters 2
+python -m paper_2507_15464_gb300.profile_case mlp --kernels 524288 --iters 3
 
 Inputs are seeded random arrays of the benchmark's shapes (the kernels'
 cost does not depend on the values); nothing is checked here.
@@ -19,13 +20,14 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["das", "das_adjoint", "tidas", "tidas_adjoint", "tidas2d",
-                                        "tidas2d_adjoint", "line"])
+                                        "tidas2d_adjoint", "line", "mlp"])
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--dtype", default="f16", choices=["f16", "f32"])
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--kz", type=int, default=16)
     ap.add_argument("--geom", default="pw128_compound")
+    ap.add_argument("--kernels", type=int, default=524288)
     a = ap.parse_args()
 
     import torch
@@ -33,7 +35,18 @@ def main():
     from tidas_workloads import presets
     g = presets.geometry(a.geom)
     gen = torch.Generator(device="cuda").manual_seed(0)
-    if a.case == "line":
+    if a.case == "mlp":
+        # fused inference of the kernel generator (untrained weights): samples
+        # uniform over its (x, z, F#, angle) domain
+        from paper_2507_15464_gb300 import generator
+        P = ops.DasPlan(g)
+        net = generator.KernelMLP()
+        lo = torch.tensor(generator.BOUNDS_LO, dtype=torch.float64, device="cuda")
+        hi = torch.tensor(generator.BOUNDS_HI, dtype=torch.float64, device="cuda")
+        u = torch.rand((a.kernels, 4), dtype=torch.float64, device="cuda", generator=gen)
+        s = lo + u * (hi - lo)
+        fn = lambda: net.infer(P, s)
+    elif a.case == "line":
         # the single-line experiment: 600 points, 192 elements, focus 25 mm
         p = dict(n_elem=192, pitch=0.3e-3, f0=5e6, fs=40e6, c=1540.0, frac_bw=0.6,
                  n_samples=2560, n_depths=600, z_first=2e-3, z_last=42e-3, z_focus=25e-3,
