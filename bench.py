@@ -258,6 +258,7 @@ def run_ours(args):
             "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
             "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x 2070 MHz" % sms,
             "work": "%.4g updates x 10 flop (cubic taps + apodization)" % updates,
+            "g_updates_s": updates / (ms * 1e-3) / 1e9,
             "timed": "whole step (das_tc_pack_kernel + das_tc_kernel)",
             "note": "issue-bound: 71 % of issue slots busy, mostly the weight-building "
                     "warps; tensor pipe 5.1 % busy (ncu)"}
@@ -362,7 +363,8 @@ def run_ours(args):
 
     # ---- FISTA deconvolution, exact vs tiDAS operator
     if not args.no_fista and rank == 0:
-        extra["fista"] = bench_fista(torch, capi, generators, args.fista_iters)
+        extra["fista"] = bench_fista(torch, capi, generators, args.fista_iters,
+                                     cpu=not args.no_cpu_baseline)
 
     # ---- single-line experiment of Section 3 (600 x 600 sweep)
     if not args.no_line and rank == 0:
@@ -443,6 +445,19 @@ def bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak, bf
     res["nrmse_vs_exact_das"] = float((out[0].double() - d).norm() / d.norm())
     res["band_2d"] = bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, d, args, stream,
                                    bf16_peak, das_ms_per_frame)
+    if not args.no_cpu_baseline:
+        # the FP64 oracle's Eq. (2.13) on 8 of the frames, all rows, host cores
+        import oracle
+        nfr = 8
+        kh = kern.double().cpu().numpy()
+        xs = refl[:nfr].double().cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.tidas_conv(kh, xs)
+        dt = time.perf_counter() - t0
+        res["oracle_cpu"] = {"kind": "oracle", "frames": nfr, "seconds": dt,
+                             "mpix_s": nfr * nz * nx / dt / 1e6,
+                             "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                             "sample": "%d of the %d frames, every row, FP64" % (nfr, TIDAS_FRAMES)}
     return res
 
 
@@ -683,7 +698,7 @@ def bench_line_reconstruction(torch, stream, E, rf, theta, eps):
     return res
 
 
-def bench_fista(torch, capi, generators, iters):
+def bench_fista(torch, capi, generators, iters, cpu=True):
     """Deconvolution workload: 1024 x 1024 reflectivity grid, 128-element array,
     11 angles; b = exact DAS of the grid's channel data + 30 dB Gaussian noise;
     `iters` FISTA iterations with the L1 prior, timed end to end, with the
@@ -739,6 +754,24 @@ def bench_fista(torch, capi, generators, iters):
                              "200 iterations (rel_err_vs_truth near 1 for any operator); "
                              "data_residual and objective_ratio show the solve"}
     res["speedup_tidas_gemm_resid_vs_exact"] = res["exact"]["seconds"] / res["tidas_gemm_resid"]["seconds"]
+    if cpu:
+        # the FP64 oracle's FISTA with the row-kernel tiDAS operator (Eq. (2.13)
+        # and its transpose) on the same data, 3 iterations on the host cores; the
+        # exact operator's FP64 synthesis of a 1024 x 1024 grid takes minutes
+        import oracle
+        from oracle import fista as ofista
+        kh = kern.double().cpu().numpy()
+        bh = b[0].double().cpu().numpy()
+        lam = res["tidas_direct"]["lambda"]
+        L = 1.01 * res["tidas_direct"]["L"]
+        n_it = 3
+        t0 = time.perf_counter()
+        ofista.fista(lambda v: oracle.tidas_conv(kh, v), lambda v: oracle.tidas_conv_adjoint(kh, v),
+                     bh, lam, L, n_it)
+        dt = time.perf_counter() - t0
+        res["oracle_cpu_tidas"] = {"kind": "oracle", "iters": n_it, "ms_per_iter": dt / n_it * 1e3,
+                                   "cores": int(os.environ.get("OMP_NUM_THREADS",
+                                                               os.cpu_count() or 1))}
     return res
 
 
