@@ -23,7 +23,7 @@
 //
 // Warp roles (12 warps, two groups):
 //  - warps 0, 1: producers of group 0 / group 1: one bulk copy per pair into
-//    the group's ring of K-step chunks (as many pairs in flight as the ring
+//    the group's ring of K-step chunks (as many rounds in flight as the ring
 //    holds).  Warp 0 also owns tensor memory.
 //  - warps 2-5 / 6-9: the builders of group 0 / group 1.  The pairs of a
 //    tile are cut into rounds of one or two consecutive pairs whose K-steps
@@ -195,9 +195,9 @@ __device__ __forceinline__ void place4(uint64_t v, int o, uint4& lo, uint4& hi) 
 }
 
 // Hand-off between group g's 128 builders and its MMA warp (160 threads):
-// a barrier that both sides wait on, once per pair, which also tells every
+// a barrier that both sides wait on, once per round, which also tells every
 // participant whether any of them has given up.  While the builders write
-// pair j + 1 the MMA warp issues pair j, so the two overlap.
+// round j + 1 the MMA warp issues round j, so the two overlap.
 __device__ __forceinline__ bool group_bar(int grp, int stop) {
     constexpr int kCount = 32 * 5;
     return grp == 0 ? named_bar_or<2>(kCount, stop) : named_bar_or<3>(kCount, stop);
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     const int Sp = packed_len(d.n_samples);
     uint8_t* sW = base;                                        // [kWTiles] weight tiles
     uint8_t* sC = base + kWTiles * kWBytes;                    // [kGroups][C] chunks
-    // group g, pair slot p: full completes when the pair's chunks have landed,
-    // empty when the pair's MMAs have finished reading its chunks and tile
+    // group g, round slot p: full completes when the round's chunks have
+    // landed, empty when its MMAs have finished reading its chunks and tile
     uint64_t* full = (uint64_t*)(sC + kGroups * C * CB);      // [kGroups][kPairSlots]
     uint64_t* empty = full + kGroups * kPairSlots;             // [kGroups][kPairSlots]
     uint64_t* done = empty + kGroups * kPairSlots;             // [kGroups]
