@@ -41,7 +41,7 @@ extern "C" {
 #define TIDAS_ERR_ARG (-1)         /* bad argument: null pointer, size, alignment, dtype */
 #define TIDAS_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
 #define TIDAS_ERR_TIMEOUT (-3)     /* a bounded device wait gave up (see tidas_device_status) */
-#define TIDAS_ERR_UNSUPPORTED (-4) /* valid request this build does not implement */
+#define TIDAS_ERR_UNSUPPORTED (-4) /* valid request the library does not implement */
 
 #define TIDAS_RF_F32 0
 #define TIDAS_RF_F16 1
