@@ -28,3 +28,20 @@ def test_mlp_gradients_match_finite_differences():
                 assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (l, idx, fd, g[idx])
     # the unused output column gets no gradient
     assert np.all(grads[-1][0][used:] == 0) and np.all(grads[-1][1][used:] == 0)
+
+
+def test_mlp_forward_matches_library_linear_layers():
+    # the forward pass against torch's CPU linear layers in FP64 (y = x W^T + b,
+    # ReLU after every layer but the last): a library routine, not a retyping
+    import torch
+    rng = np.random.default_rng(1)
+    sizes = [(16, 4), (12, 16), (12, 12), (5, 12)]
+    params = [(rng.standard_normal(s) * 0.5, rng.standard_normal(s[0]) * 0.2) for s in sizes]
+    x = rng.standard_normal((9, 4))
+    acts = mlp.forward(params, x)
+    h = torch.from_numpy(x)
+    for l, (W, b) in enumerate(params):
+        h = torch.nn.functional.linear(h, torch.from_numpy(W), torch.from_numpy(b))
+        if l < len(params) - 1:
+            h = torch.relu(h)
+        np.testing.assert_allclose(acts[l + 1], h.numpy(), rtol=1e-13, atol=1e-14)
