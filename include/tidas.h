@@ -87,8 +87,9 @@ int das_plan_create(const das_params* params, das_plan* out_plan);
 int das_plan_destroy(das_plan plan);
 
 /* Plan options.  DAS_OPT_TENSOR_CORES: 1 (default) runs das_forward of FP16
- * plans on the tcgen05 tensor cores when n_frames >= 16 and every
- * (32 x 4-pixel tile, angle, element) window of samples fits 64 samples
+ * plans on the tcgen05 tensor cores when n_frames >= 16, every
+ * (32 x 4-pixel tile, angle, element) window of samples fits 64 samples and
+ * every window in use starts within 16376 samples of the record's start
  * (checked when the plan is built); 0 keeps every batch on CUDA cores.  The
  * tensor-core path rounds the apodized interpolation weights to FP16
  * (relative 2^-11).  It first repacks the batch into a staging buffer that
