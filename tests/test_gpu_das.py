@@ -141,6 +141,7 @@ def test_das_full_batch_fp16_sampled_frames():
     img = host(P16.forward(x))            # tensor cores
     P16.set_tensor_cores(False)
     img_cc = host(P16.forward(x))         # CUDA cores
+    assert not np.array_equal(img, img_cc)
     rng = np.random.default_rng(9)
     for f in (0, 37, B - 1):
         pix = rng.choice(g["nx"] * g["nz"], 600, replace=False)
@@ -169,6 +170,8 @@ def test_das_tensor_core_path(name, nf, over):
     P16.set_tensor_cores(False)
     img_cc = host(P16.forward(x))
     assert rel_l2(img, img_cc) <= TOL_TC
+    # FP16 weights against FP32 ones: equal images would mean no tensor cores ran
+    assert not np.array_equal(img, img_cc)
     rng = np.random.default_rng(10)
     for f in (0, nf - 1):
         pix = rng.choice(g["nx"] * g["nz"], min(800, g["nx"] * g["nz"]), replace=False)
