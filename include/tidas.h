@@ -27,6 +27,10 @@
  *  - Channel data rf: [n_frames][n_angles][n_elem][n_samples], float32 or
  *    IEEE half (params.rf_dtype).  Images and reflectivity maps:
  *    [n_frames][nz][nx] float32 (x contiguous).
+ *  - Counts (n_frames, grid and kernel sizes) must be >= 1; a zero count is
+ *    TIDAS_ERR_ARG.  The one empty input that is valid is a scene without
+ *    scatterers (das_synthesize with n_scat = 0, pos and amp may be NULL),
+ *    whose channel data are all zero.
  */
 #ifndef TIDAS_H
 #define TIDAS_H

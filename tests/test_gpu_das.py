@@ -56,6 +56,18 @@ def test_synthesize_single_frame_real():
     assert rel_l2(host(rf)[0], ref) <= TOL32
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_synthesize_zero_scatterers_gives_zero_data(dtype):
+    # the empty scene: no scatterer, every channel sample overwritten with 0
+    g = presets.geometry("pw64_single")
+    P = plan(g, dtype)
+    pos = torch.zeros((2, 0, 2), dtype=torch.float64, device="cuda")
+    amp = torch.zeros((2, 0, 2), dtype=torch.float32, device="cuda")
+    out = torch.full(P.rf_shape(2), 7.0, dtype=dtype, device="cuda")
+    rf = host(P.synthesize(pos, amp, out=out))
+    assert rf.shape == (2, 1, 64, g["n_samples"]) and not rf.any()
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
 def test_synthesize_compound_complex(dtype):
     g = presets.geometry("pw128_compound")
