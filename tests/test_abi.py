@@ -119,6 +119,17 @@ def test_null_arguments_are_rejected_before_any_launch():
     assert e.value.code == capi.TIDAS_ERR_ARG
 
 
+def test_zero_counts_are_argument_errors():
+    # empty batches and grids are rejected before anything is enqueued (the
+    # pointers below are never dereferenced: validation fails first)
+    for args in ((16, 31, 8, 8, 16, 16, 0, capi.VARIANT_DIRECT),   # no frames
+                 (16, 31, 0, 8, 16, 16, 1, capi.VARIANT_DIRECT),   # no rows
+                 (16, 0, 8, 8, 16, 16, 1, capi.VARIANT_DIRECT)):   # no taps
+        with pytest.raises(capi.TidasError) as e:
+            capi.tidas_forward(*args)
+        assert e.value.code == capi.TIDAS_ERR_ARG
+
+
 def test_band_workspace_size():
     # (rows x frame tiles x (2 per column tile + 2) chunks) x 16 KB for the
     # GEMM variant of the 2D band calls; none for the direct variant
