@@ -68,9 +68,26 @@ def line_case():
             "params": p, "eps": eps, "pairs": rows}
 
 
+def band_case():
+    # 2D band kernels (the PSF's axial extent kept, the paper's 2D outlook of
+    # Section 4) and the band form of Eq. (2.13) on a small seeded map
+    from tidas_workloads import generators
+    g = presets.toy(n_elem=16, nx=24, nz=8, n_samples=256, angles_deg=(0.0,), fnum=1.5,
+                    z0=3.0e-3, dz=0.1e-3, dx=0.1e-3, x0=-1.2e-3)
+    O = oracle.Oracle(g)
+    kz, taps = 3, 9
+    k = O.psf_patches(kz, taps)
+    refl = generators.bernoulli_normal((g["nz"], g["nx"]), 0.3, (9,))
+    y = oracle.tidas_conv2d(k.astype(np.float32).astype(np.float64), refl)
+    return {"cite": "Eq. (2.6)-(2.7) PSF of a unit scatterer kept over kz rows; Eq. (2.13) "
+                    "summed over the band rows",
+            "geometry": g, "kz": kz, "taps": taps, "kernels": k.tolist(),
+            "refl": refl.tolist(), "band_conv_of_fp32_rounded_kernels": y.tolist()}
+
+
 def main():
     for name, fn in (("das_toy", das_case), ("row_kernels_toy", kernel_case),
-                     ("line_sweep_toy", line_case)):
+                     ("line_sweep_toy", line_case), ("band_toy", band_case)):
         with open(os.path.join(HERE, name + ".json"), "w") as f:
             json.dump(fn(), f, indent=1)
         print("wrote", name)

@@ -45,6 +45,16 @@ def test_oracle_reproduces_stored_kernels_and_line_pairs():
         assert eg == pytest.approx(row["err_global"], rel=1e-9, abs=1e-14)
 
 
+def test_oracle_reproduces_stored_band_kernels_and_convolution():
+    import oracle
+    B = load("band_toy")
+    k = oracle.Oracle(B["geometry"]).psf_patches(B["kz"], B["taps"])
+    np.testing.assert_allclose(k, B["kernels"], rtol=1e-12, atol=1e-15)
+    y = oracle.tidas_conv2d(np.array(B["kernels"], np.float32).astype(np.float64),
+                            np.array(B["refl"]))
+    np.testing.assert_allclose(y, B["band_conv_of_fp32_rounded_kernels"], rtol=1e-12, atol=1e-14)
+
+
 # --------------------------------------------------------------------- GPU
 @pytest.mark.gpu
 def test_gpu_matches_stored_das_case():
@@ -81,3 +91,18 @@ def test_gpu_matches_stored_kernels_and_line_pairs():
         assert th[s, r] == pytest.approx(row["theta"], rel=1e-4)
         assert el[s, r] == pytest.approx(row["err_local"], abs=1e-4)
         assert eg[s, r] == pytest.approx(row["err_global"], abs=1e-4)
+
+
+@pytest.mark.gpu
+def test_gpu_matches_stored_band_kernels_and_convolution():
+    from .gpu_helpers import host, rel_l2, require_gpu, torch
+    require_gpu()
+    from paper_2507_15464_gb300 import capi, ops
+    from paper_2507_15464_gb300.ops import DasPlan
+    B = load("band_toy")
+    k = DasPlan(B["geometry"]).fit_kernels_2d(B["kz"], B["taps"])
+    assert rel_l2(host(k), np.array(B["kernels"])) <= 1e-5
+    kern = torch.tensor(B["kernels"], dtype=torch.float32, device="cuda")
+    refl = torch.tensor(B["refl"], dtype=torch.float32, device="cuda")[None]
+    y = ops.tidas_forward_2d(kern, refl, variant=capi.VARIANT_DIRECT)
+    assert rel_l2(host(y)[0], np.array(B["band_conv_of_fp32_rounded_kernels"])) <= 1e-5
