@@ -57,6 +57,7 @@ def das(rf, plan: DasPlan):
 
 
 def synthesize_grid(refl, plan: DasPlan):
+    """Eq. (2.1) on the pixel grid with autograd (backward = das_synthesize_adjoint)."""
     return _SynthGridFn.apply(refl, plan)
 
 
@@ -74,6 +75,9 @@ def tidas(refl, kernels, variant=capi.VARIANT_DIRECT):
 
 # ------------------------------------------------------------- operators
 class TidasOperator:
+    """H = tiDAS with row kernels (Eq. (2.13)) for FISTA: forward(x, out) and
+    adjoint(y, out) on [B, nz, nx] FP32 tensors."""
+
     def __init__(self, kernels, variant=capi.VARIANT_DIRECT):
         self.kernels, self.variant = kernels, variant
 
@@ -102,6 +106,9 @@ class TidasBandOperator:
 
 
 class ExactOperator:
+    """H = DAS of the channel data a reflectivity map produces (das_forward o
+    das_synthesize_grid), with its exact transpose; FP32 plans."""
+
     def __init__(self, plan: DasPlan, frames=1):
         if plan.rf_dtype != torch.float32:
             raise ValueError("the exact operator needs an FP32 plan")
@@ -126,12 +133,14 @@ def dot(a, b):
 
 
 def asum(a):
+    """FP64 sum of |a| of a float32 CUDA tensor (the L1 norm in the objective)."""
     out = torch.empty((), dtype=torch.float64, device=a.device)
     capi.tidas_asum(_ptr(a), a.numel(), _ptr(out), _stream())
     return out
 
 
 def axpby(alpha, a, beta, b, out):
+    """out = alpha a + beta b on float32 CUDA tensors."""
     capi.tidas_axpby(_ptr(a), _ptr(b), _ptr(out), a.numel(), alpha, beta, _stream())
     return out
 

@@ -60,6 +60,12 @@ def _f32(shape):
 
 
 class KernelMLP:
+    """The kernel generator 4 -> 256 -> 256 -> 256 -> 63 (ReLU between layers):
+    FP32 master weights with BF16 copies for the tensor cores, AdamW training
+    (fit), fused inference (infer) and the layer-by-layer reference path
+    (infer_layers).  `params` is a list of (W [out, in], b [out]) float32 arrays,
+    seeded by init_params() when omitted."""
+
     def __init__(self, params=None, batch=256):
         params = params or init_params()
         self.B = batch
@@ -107,11 +113,15 @@ class KernelMLP:
 
     # ------------------------------------------------------------ primitives
     def encode(self, samples, out16):
+        """(x, z, F#, angle) samples [n, 4] float64 -> inputs [n, 64] BF16 in [-1, 1]
+        (the four features, zero padding)."""
         capi.call("tidas_encode", _ptr(samples), samples.shape[0], _ptr(self.lo), _ptr(self.hi),
                   _ptr(out16), _stream())
 
     @staticmethod
     def gemm(A, B, M, N, K, bias, relu, c32, c16, ldc):
+        """C = act(A B^T + bias) on the tensor cores, BF16 A [M, K] and B [N, K],
+        FP32 (c32) and / or BF16 (c16) outputs with leading dimension ldc."""
         capi.call("tidas_gemm_bf16", _ptr(A), _ptr(B), M, N, K,
                   _ptr(bias) if bias is not None else None, 1 if relu else 0,
                   _ptr(c32) if c32 is not None else None,

@@ -58,6 +58,7 @@ class DasPlan:
         capi.call("das_plan_set_option", self.handle, 1, 1 if on else 0)
 
     def close(self):
+        """Destroy the plan (frees its device tables; synchronises the device)."""
         if self.handle:
             capi.das_plan_destroy(self.handle)
             self.handle = None
@@ -70,9 +71,11 @@ class DasPlan:
 
     # shapes
     def rf_shape(self, nf):
+        """Shape of nf frames of channel data: (frames, angles, elements, samples)."""
         return (nf, self.A, self.N, self.S)
 
     def img_shape(self, nf):
+        """Shape of nf images or reflectivity maps: (frames, nz, nx)."""
         return (nf, self.nz, self.nx)
 
     # operations
@@ -87,6 +90,8 @@ class DasPlan:
         return out
 
     def synthesize_grid(self, refl, out=None):
+        """Eq. (2.1) for reflectivities on the pixel centres: refl [B, nz, nx] FP32 ->
+        rf [B, A, N, S] FP32 (the forward operator of deconvolution)."""
         nf = refl.shape[0]
         _need(refl, torch.float32, self.img_shape(nf), "refl")
         out = out if out is not None else torch.empty(self.rf_shape(nf), dtype=torch.float32,
@@ -95,6 +100,7 @@ class DasPlan:
         return out
 
     def synthesize_adjoint(self, rf, out=None):
+        """Transpose of synthesize_grid: rf [B, A, N, S] FP32 -> refl [B, nz, nx]."""
         nf = rf.shape[0]
         _need(rf, torch.float32, self.rf_shape(nf), "rf")
         out = out if out is not None else torch.empty(self.img_shape(nf), dtype=torch.float32,
@@ -103,6 +109,8 @@ class DasPlan:
         return out
 
     def forward(self, rf, out=None):
+        """Eq. (2.2) Delay-and-Sum: rf [B, A, N, S] (the plan's dtype) -> img [B, nz, nx]
+        FP32.  FP16 batches of >= 16 frames run on the tensor cores."""
         nf = rf.shape[0]
         _need(rf, self.rf_dtype, self.rf_shape(nf), "rf")
         out = out if out is not None else torch.empty(self.img_shape(nf), dtype=torch.float32,
@@ -111,6 +119,7 @@ class DasPlan:
         return out
 
     def adjoint(self, img, out=None):
+        """Transpose of forward for FP32 plans: img [B, nz, nx] -> rf [B, A, N, S]."""
         nf = img.shape[0]
         _need(img, torch.float32, self.img_shape(nf), "img")
         out = out if out is not None else torch.empty(self.rf_shape(nf), dtype=torch.float32,
@@ -119,12 +128,15 @@ class DasPlan:
         return out
 
     def delay_table(self, angle, device="cuda"):
+        """Bit-exact FP64 delay split of one angle: (idx int32, frac FP32), [nz, nx, N]."""
         idx = torch.empty((self.nz, self.nx, self.N), dtype=torch.int32, device=device)
         frac = torch.empty((self.nz, self.nx, self.N), dtype=torch.float32, device=device)
         capi.das_delay_table(self.handle, angle, _ptr(idx), _ptr(frac), _stream())
         return idx, frac
 
     def fit_kernels(self, taps, ref_stride=1, device="cuda"):
+        """Row kernels of Eq. (2.13) from exact PSF rows (Eq. (2.6)-(2.7)) and their
+        least-squares weights theta (Eq. (2.12)): (kernels [nz, taps], theta [nz])."""
         k = torch.empty((self.nz, taps), dtype=torch.float32, device=device)
         th = torch.empty((self.nz,), dtype=torch.float32, device=device)
         capi.tidas_fit_kernels(self.handle, taps, ref_stride, _ptr(k), _ptr(th), _stream())
@@ -207,6 +219,7 @@ def tidas_forward(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
 
 
 def tidas_adjoint(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
+    """Transpose of tidas_forward (correlation with each row's kernel)."""
     return _tidas(capi.tidas_adjoint, kernels, img, variant, out)
 
 
@@ -239,6 +252,7 @@ def tidas_forward_2d(kernels, refl, variant=capi.VARIANT_DIRECT, out=None, works
 
 
 def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None, workspace=None):
+    """Transpose of tidas_forward_2d: img [B, nz, nx] -> refl [B, nz, nx]."""
     return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out, workspace)
 
 
@@ -258,9 +272,12 @@ class LineExperiment:
         return capi.tidas_line_window(self.P)
 
     def depth(self, i):
+        """Depth in metres of line point i (points evenly spaced from z_first to z_last)."""
         return self.P.z_first + (self.P.z_last - self.P.z_first) * i / (self.D - 1)
 
     def synthesize(self, r_first=0, n_scat=None, out=None, device="cuda"):
+        """Channel data [n_scat, N, S] of a unit scatterer on each line point from
+        r_first on, under the focused transmit (Eq. (2.1))."""
         n_scat = self.D - r_first if n_scat is None else n_scat
         out = out if out is not None else torch.empty((n_scat, self.N, self.S),
                                                       dtype=torch.float32, device=device)
@@ -269,6 +286,7 @@ class LineExperiment:
         return out
 
     def das_lines(self, rf, out=None):
+        """DAS lines [n, n_depths] of channel data [n, N, S] (Eq. (2.7) with dynamic focus)."""
         n = rf.shape[0]
         _need(rf, torch.float32, (n, self.N, self.S), "rf")
         out = out if out is not None else torch.empty((n, self.D), dtype=torch.float32,
