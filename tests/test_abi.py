@@ -148,3 +148,19 @@ def test_line_window_is_half_the_envelope_fwhm():
         p = paper_line(f0=f0)
         eps = capi.tidas_line_window(capi.line_params(**p))
         assert eps == pytest.approx(LineOracle(p).eps(), rel=1e-15)
+
+
+def test_tensor_api_refuses_host_tensors():
+    # no CPU fallback: the torch-level wrappers hand device pointers to the C ABI
+    # and raise on host tensors instead of computing anything on the CPU
+    import torch
+    from paper_2507_15464_gb300 import deconv, ops
+    k = torch.zeros((8, 31), dtype=torch.float32)
+    x = torch.zeros((1, 8, 16), dtype=torch.float32)
+    with pytest.raises(ValueError, match="GPU"):
+        ops.tidas_forward(k, x, out=torch.empty_like(x))
+    k2 = torch.zeros((8, 3, 31), dtype=torch.float32)
+    with pytest.raises(ValueError, match="GPU"):
+        ops.tidas_forward_2d(k2, x, out=torch.empty_like(x))
+    with pytest.raises(ValueError, match="GPU"):
+        deconv.dot(x, x)
