@@ -168,8 +168,7 @@ def test_tensor_api_refuses_host_tensors():
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     # without libtidas.so the bindings raise; nothing substitutes for the kernels
-    from paper_2507_15464_gb300 import _build
     monkeypatch.setattr(capi, "_lib", None)
-    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libtidas.so"))
+    monkeypatch.setattr(capi._build, "LIB", str(tmp_path / "libtidas.so"))
     with pytest.raises(OSError, match="not been built"):
         capi.load(build_if_missing=False)
