@@ -64,6 +64,8 @@ def lib():
             "orc_tidas_conv_adjoint": (None, [ctypes.c_int] * 4 + [_D, _D, _D]),
             "orc_tidas_conv2d": (None, [ctypes.c_int] * 6 + [_D, _D, _D]),
             "orc_tidas_conv2d_adjoint": (None, [ctypes.c_int] * 6 + [_D, _D, _D]),
+            "orc_tidas_conv_varying": (None, [ctypes.c_int] * 6 + [_D, _D, _D]),
+            "orc_tidas_conv_varying_adjoint": (None, [ctypes.c_int] * 6 + [_D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -342,6 +344,43 @@ def tidas_conv2d_adjoint(kernels, y):
     r = np.empty_like(y)
     lib().orc_tidas_conv2d_adjoint(nz, y.shape[1], kz, taps, kz // 2, taps // 2, _dp(kernels),
                                    _dp(y), _dp(r))
+    return r
+
+
+def _varying_shape(kernels):
+    """[nz, nx, taps] (row kernels) or [nz, nx, kz, taps] (band kernels) ->
+    the 4-D array and its sizes."""
+    kernels = _f64(kernels)
+    if kernels.ndim == 3:
+        kernels = kernels[:, :, None, :]
+    nz, nx, kz, taps = kernels.shape
+    return np.ascontiguousarray(kernels), nz, nx, kz, taps
+
+
+def tidas_conv_varying(kernels, r):
+    """Eq. (2.13) with a kernel per pixel: every pixel (j, s) of r adds r[j][s]
+    times its own single-scatterer image kernels[j][s] (taps columns, or kz
+    rows x taps columns, centred on the pixel).  [nz, nx] or [B, nz, nx]."""
+    k, nz, nx, kz, taps = _varying_shape(kernels)
+    r = _f64(r)
+    if r.ndim == 3:
+        return np.stack([tidas_conv_varying(k, x) for x in r])
+    assert r.shape == (nz, nx)
+    y = np.empty_like(r)
+    lib().orc_tidas_conv_varying(nz, nx, kz, taps, kz // 2, taps // 2, _dp(k), _dp(r), _dp(y))
+    return y
+
+
+def tidas_conv_varying_adjoint(kernels, y):
+    """Transpose of tidas_conv_varying: each pixel correlates y with its own kernel."""
+    k, nz, nx, kz, taps = _varying_shape(kernels)
+    y = _f64(y)
+    if y.ndim == 3:
+        return np.stack([tidas_conv_varying_adjoint(k, x) for x in y])
+    assert y.shape == (nz, nx)
+    r = np.empty_like(y)
+    lib().orc_tidas_conv_varying_adjoint(nz, nx, kz, taps, kz // 2, taps // 2, _dp(k), _dp(y),
+                                         _dp(r))
     return r
 
 

@@ -371,6 +371,60 @@ void orc_tidas_conv2d_adjoint(int nz, int nx, int kz, int taps, int cz, int cx,
         }
 }
 
+/* Spatially varying kernels (Eq. (2.13) with the kernel of every pixel its
+ * own single-scatterer image, Eq. (2.6)-(2.7)): kernels[j][s][u][t] is the
+ * image of a unit scatterer on pixel (row j, column s) at output row
+ * j + u - cz, column s + t - cx.  Born superposition (Eq. (2.1) is linear in
+ * the reflectivity, Eq. (2.2) is linear in the data) adds the images of all
+ * pixels of r, each scaled by its reflectivity:
+ *   y[i][x] = sum_{u, t} kernels[j][s][u][t] * r[j][s],
+ *             j = i - u + cz,  s = x - t + cx,
+ * rows and columns outside the grid contributing nothing.  The kernel is the
+ * one of the INPUT pixel (j, s), the scatterer.  kz = 1, cz = 0 is the
+ * row-wise form; with kernels equal along every row it is orc_tidas_conv2d
+ * term for term (same loop order). */
+void orc_tidas_conv_varying(int nz, int nx, int kz, int taps, int cz, int cx,
+                            const double* kernels, const double* r, double* y) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < nz; ++i)
+        for (int x = 0; x < nx; ++x) {
+            double acc = 0.0;
+            for (int u = 0; u < kz; ++u) {
+                int j = i - u + cz;
+                if (j < 0 || j >= nz) continue;
+                for (int t = 0; t < taps; ++t) {
+                    int s = x - t + cx;
+                    if (s < 0 || s >= nx) continue;
+                    acc += kernels[(((size_t)j * nx + s) * kz + u) * taps + t] *
+                           r[(size_t)j * nx + s];
+                }
+            }
+            y[(size_t)i * nx + x] = acc;
+        }
+}
+/* Transpose of orc_tidas_conv_varying: every pixel correlates the output with
+ * its own kernel,
+ *   r[j][s] = sum_{u, t} kernels[j][s][u][t] * y[j + u - cz][s + t - cx]. */
+void orc_tidas_conv_varying_adjoint(int nz, int nx, int kz, int taps, int cz, int cx,
+                                    const double* kernels, const double* y, double* r) {
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < nz; ++j)
+        for (int s = 0; s < nx; ++s) {
+            double acc = 0.0;
+            for (int u = 0; u < kz; ++u) {
+                int i = j + u - cz;
+                if (i < 0 || i >= nz) continue;
+                for (int t = 0; t < taps; ++t) {
+                    int x = s + t - cx;
+                    if (x < 0 || x >= nx) continue;
+                    acc += kernels[(((size_t)j * nx + s) * kz + u) * taps + t] *
+                           y[(size_t)i * nx + x];
+                }
+            }
+            r[(size_t)j * nx + s] = acc;
+        }
+}
+
 /* =========================================================================
  * Single-line experiment of Section 3 (focused transmit, one image line on
  * the array axis), in the channel domain of Eq. (2.8) -- Eq. (2.13).

@@ -435,6 +435,81 @@ def test_psf_patch_reproduces_exact_image():
         np.testing.assert_allclose(pat[n][kz // 2], psf[n], rtol=1e-13, atol=1e-13)
 
 
+# ------------------------------------------ spatially varying (per-pixel) kernels
+def test_tidas_conv_varying_with_equal_kernels_is_the_shift_invariant_form():
+    # the same kernel at every pixel of a row: term for term the row-wise and
+    # the band convolutions (same loop order, so bit for bit)
+    import oracle
+    rng = np.random.default_rng(20)
+    nz, nx = 7, 33
+    h1 = rng.standard_normal((nz, 9))
+    h2 = rng.standard_normal((nz, 5, 9))
+    r = rng.standard_normal((2, nz, nx))
+    k1 = np.ascontiguousarray(np.broadcast_to(h1[:, None, :], (nz, nx, 9)))
+    k2 = np.ascontiguousarray(np.broadcast_to(h2[:, None], (nz, nx, 5, 9)))
+    np.testing.assert_array_equal(oracle.tidas_conv_varying(k1, r), oracle.tidas_conv(h1, r))
+    np.testing.assert_array_equal(oracle.tidas_conv_varying(k2, r), oracle.tidas_conv2d(h2, r))
+
+
+@pytest.mark.parametrize("kz,taps", [(1, 7), (1, 8), (5, 7), (4, 6)])
+def test_tidas_conv_varying_superposes_each_pixels_own_kernel(kz, taps):
+    # Born superposition written independently of the oracle's loop: every
+    # input pixel (j, s) adds r[j][s] times ITS OWN kernel, placed with its
+    # centre on the pixel.  A unit reflector returns exactly its kernel, so the
+    # kernel of the output pixel (the other possible reading) would fail.
+    import oracle
+    rng = np.random.default_rng(21)
+    nz, nx = 9, 23
+    k = rng.standard_normal((nz, nx, kz, taps))
+    r = rng.standard_normal((nz, nx))
+    cz, cx = kz // 2, taps // 2
+    want = np.zeros((nz + 2 * kz, nx + 2 * taps))  # padded canvas
+    for j in range(nz):
+        for s in range(nx):
+            i0, x0 = j - cz + kz, s - cx + taps
+            want[i0:i0 + kz, x0:x0 + taps] += r[j, s] * k[j, s]
+    want = want[kz:kz + nz, taps:taps + nx]
+    got = oracle.tidas_conv_varying(k if kz > 1 else k[:, :, 0], r)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    e = np.zeros((nz, nx))
+    e[4, 11] = 1.0
+    y = oracle.tidas_conv_varying(k, e)
+    for u in range(kz):
+        np.testing.assert_array_equal(y[4 + u - cz, 11 - cx:11 - cx + taps], k[4, 11, u])
+    mask = np.ones((nz, nx), bool)
+    mask[4 - cz:4 - cz + kz, 11 - cx:11 - cx + taps] = False
+    assert not y[mask].any()
+    # adjoint identity
+    v = rng.standard_normal((nz, nx))
+    lhs = np.vdot(oracle.tidas_conv_varying(k, r), v)
+    rhs = np.vdot(r, oracle.tidas_conv_varying_adjoint(k, v))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_exact_per_pixel_psfs_reproduce_das():
+    # Eq. (2.1) and Eq. (2.2) are linear, so with every pixel's exact
+    # single-scatterer image as its kernel (support covering the whole grid),
+    # the varying convolution of a reflectivity map IS the DAS image of its
+    # synthesised channel data.  A steered wave and a finite F# make the
+    # images differ from pixel to pixel.
+    import oracle
+    g = presets.toy(n_elem=10, nx=6, nz=5, n_samples=160, angles_deg=(7.0,), fnum=1.2)
+    o = O(g)
+    kz, taps = 2 * g["nz"] - 1, 2 * g["nx"] - 1
+    cz, cx = kz // 2, taps // 2
+    k = np.zeros((g["nz"], g["nx"], kz, taps))
+    for j in range(g["nz"]):
+        for s in range(g["nx"]):
+            img = o.das(o.synthesize([[o.pix_x(s), o.pix_z(j)]], [[1.0, 0.0]]))
+            k[j, s, cz - j:cz - j + g["nz"], cx - s:cx - s + g["nx"]] = img
+    # the images do vary across the grid
+    assert np.abs(k[0, 0] - k[4, 5]).max() > 0.1 * np.abs(k).max()
+    r = np.random.default_rng(22).standard_normal((g["nz"], g["nx"]))
+    das = o.das(o.synth_grid(r))
+    y = oracle.tidas_conv_varying(k, r)
+    np.testing.assert_allclose(y, das, rtol=0, atol=1e-12 * np.abs(das).max())
+
+
 def test_fwhm_of_gaussian():
     import oracle
     x = np.arange(-50, 51, dtype=np.float64)
