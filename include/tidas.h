@@ -141,8 +141,10 @@ int das_forward(das_plan plan, const void* rf, float* img, int32_t n_frames, voi
 
 /* Transpose of das_forward (B^T), for FP32 channel data plans:
  *   img [n_frames][nz][nx] float32 -> rf [n_frames][n_angles][n_elem][n_samples] float32
- * Each channel sample gathers w * (interpolation weight) * img from the
- * pixels that read it; the result is deterministic. */
+ * Each channel sample receives w * (interpolation weight) * img from the
+ * pixels that read it.  The contributions are summed with shared-memory
+ * atomics, so their order is not fixed: repeated calls agree to FP32
+ * rounding, not necessarily bit for bit. */
 int das_adjoint(das_plan plan, const float* img, float* rf, int32_t n_frames, void* stream);
 
 /* Delay-index table of one angle, the integer/fraction split of
@@ -322,9 +324,12 @@ int tidas_dot(const float* a, const float* b, int64_t n, double* out, void* stre
  * fixed 32 KB device array inside the library (held on every GPU that loads
  * it until exit), so n is limited to 16,777,216 elements; larger n returns
  * TIDAS_ERR_ARG before anything is enqueued.  The first call on each device
- * looks up the array's device address (with that device current); make it
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU, for example on two streams, race and give wrong sums. */
+ * looks up the array's device address (with that device current) and keeps
+ * it; make that call before any stream capture.  A cudaDeviceReset destroys
+ * the module that holds the array, so the kept address is then stale: do not
+ * call this entry point after resetting a device it was used on.  All calls
+ * share the array: calls that overlap on the GPU, for example on two
+ * streams, race and give wrong sums. */
 int tidas_dot_noalloc(const float* a, const float* b, int64_t n, double* out, void* stream);
 
 /* *out (DEVICE double) = sum_i |a[i]|, FP64; scratch as tidas_dot. */
@@ -417,10 +422,32 @@ int tidas_mlp_infer(const double* samples, int64_t n, const float* lo4, const fl
                     const void* const* w16, const float* const* bias, const float* scale,
                     float* out, int32_t ldo, void* stream);
 
-/* Eq. (2.13) with a kernel per pixel: img[f][z][x] = sum_t h[z][x][t] *
- * refl[f][z][x - t + taps/2]; kernels [nz * nx][ld], taps <= 64. */
+/* Spatially varying tiDAS: Eq. (2.13) with a kernel per pixel, the kernel of
+ * pixel (j, s) being the single-scatterer image of that pixel (Eq. (2.6)-
+ * (2.7)) over kz rows x taps columns centred on it.  Eq. (2.1) and (2.2) are
+ * linear in the reflectivity, so every pixel of refl adds its own image,
+ * scaled by its reflectivity (the kernel is the INPUT pixel's):
+ *   img[f][i][x] = sum_{u, t} K[j][s][u][t] * refl[f][j][s],
+ *                  j = i - u + kz/2,  s = x - t + taps/2,
+ * rows and columns outside the grid contributing nothing.
+ *   kernels  [nz][nx][kz][ld] float32, element (j, s, u, t) at
+ *            ((j nx + s) kz + u) ld + t; 1 <= taps <= 64, ld >= taps,
+ *            1 <= kz <= 64
+ *   refl     [n_frames][nz][nx] float32 (variant TIDAS_VARIANT_DIRECT: FP32
+ *            CUDA cores, the only variant of these calls)
+ *   img      [n_frames][nz][nx] float32 (overwritten)
+ * tidas_forward_varying is the row form (kz = 1, kernels [nz * nx][ld]).
+ * tidas_adjoint_varying_2d is the transpose: each pixel correlates img with
+ * its own kernel, refl[f][j][s] = sum_{u,t} K[j][s][u][t] img[f][j+u-kz/2][s+t-taps/2].
+ * Other variants return TIDAS_ERR_UNSUPPORTED.  Sums run in a fixed order. */
 int tidas_forward_varying(const float* kernels, int32_t ld, int32_t taps, int32_t nz, int32_t nx,
                           const float* refl, float* img, int32_t n_frames, void* stream);
+int tidas_forward_varying_2d(const float* kernels, int32_t ld, int32_t kz, int32_t taps,
+                             int32_t nz, int32_t nx, const void* refl, float* img,
+                             int32_t n_frames, int32_t variant, void* stream);
+int tidas_adjoint_varying_2d(const float* kernels, int32_t ld, int32_t kz, int32_t taps,
+                             int32_t nz, int32_t nx, const void* img, float* refl,
+                             int32_t n_frames, int32_t variant, void* stream);
 
 /* Per-pixel NRMSE of learned vs exact kernels (nrmse[p], may be NULL); out
  * takes the exact kernel where the NRMSE exceeds thresh, else the learned one. */

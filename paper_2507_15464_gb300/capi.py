@@ -85,6 +85,8 @@ _SIG = {
     "tidas_forward_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _S, _P],
     "tidas_adjoint_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _S, _P],
     "tidas_forward_varying": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
+    "tidas_forward_varying_2d": [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P],
+    "tidas_adjoint_varying_2d": [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
     "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],
     "tidas_band_workspace_bytes": [_I, _I, _I, _I],
@@ -196,6 +198,18 @@ def tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant, wo
                      workspace_bytes=0, stream=0):
     return _check(load().tidas_adjoint_2d(kernels, kz, taps, nz, nx, img, refl, n_frames, variant,
                                           workspace, workspace_bytes, stream))
+
+
+def tidas_forward_varying_2d(kernels, ld, kz, taps, nz, nx, refl, img, n_frames, variant,
+                             stream=0):
+    return _check(load().tidas_forward_varying_2d(kernels, ld, kz, taps, nz, nx, refl, img,
+                                                  n_frames, variant, stream))
+
+
+def tidas_adjoint_varying_2d(kernels, ld, kz, taps, nz, nx, img, refl, n_frames, variant,
+                             stream=0):
+    return _check(load().tidas_adjoint_varying_2d(kernels, ld, kz, taps, nz, nx, img, refl,
+                                                  n_frames, variant, stream))
 
 
 def tidas_line_synthesize(p, r_first, n_scat, rf, stream=0):

@@ -241,12 +241,12 @@ int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaS
     size_t smem = (size_t)d.n_samples * sizeof(float);
     dim3 grid(d.n_elem, d.n_angles, nf);
     if (d.interp == TIDAS_INTERP_CUBIC) {
-        cudaFuncSetAttribute(das_adjoint_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        TIDAS_CUDA(cudaFuncSetAttribute(das_adjoint_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
         das_adjoint_kernel<1><<<grid, 256, smem, st>>>(d, img, rf);
     } else {
-        cudaFuncSetAttribute(das_adjoint_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        TIDAS_CUDA(cudaFuncSetAttribute(das_adjoint_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
         das_adjoint_kernel<0><<<grid, 256, smem, st>>>(d, img, rf);
     }
     return check_launch("das_adjoint_kernel");
@@ -338,14 +338,14 @@ int launch_synthesize(const Plan& P, const double* pos, const float* amp, int n_
     size_t smem = (size_t)d.n_samples * sizeof(float);
     dim3 grid(d.n_elem, d.n_angles, nf);
     if (d.rf_dtype == TIDAS_RF_F16) {
-        cudaFuncSetAttribute(synth_points_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        TIDAS_CUDA(cudaFuncSetAttribute(synth_points_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
         synth_points_kernel<__half><<<grid, 256, smem, st>>>(d, pos, amp, n_scat, P.d_sncs,
                                                             (__half*)rf, P.p.c, P.p.t0, P.p.fs,
                                                             P.p.pitch);
     } else {
-        cudaFuncSetAttribute(synth_points_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        TIDAS_CUDA(cudaFuncSetAttribute(synth_points_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
         synth_points_kernel<float><<<grid, 256, smem, st>>>(d, pos, amp, n_scat, P.d_sncs,
                                                            (float*)rf, P.p.c, P.p.t0, P.p.fs,
                                                            P.p.pitch);
@@ -521,8 +521,12 @@ int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, 
             refl, reflT, d.nz, d.nx);
         int rc = check_launch("transpose_grid_kernel");
         if (rc == TIDAS_OK) {
-            cudaFuncSetAttribute(synth_grid_gather_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g);
+            rc = check_cuda(cudaFuncSetAttribute(synth_grid_gather_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem_g),
+                            "cudaFuncSetAttribute(synth_grid_gather_kernel)");
+        }
+        if (rc == TIDAS_OK) {
             synth_grid_gather_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem_g, st>>>(d, reflT,
                                                                                         rf);
             rc = check_launch("synth_grid_gather_kernel");
@@ -531,7 +535,7 @@ int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, 
         return rc;
     }
     size_t smem = (size_t)d.n_samples * sizeof(float);
-    cudaFuncSetAttribute(synth_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TIDAS_CUDA(cudaFuncSetAttribute(synth_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     synth_grid_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem, st>>>(d, refl, rf);
     return check_launch("synth_grid_kernel");
 }

@@ -738,7 +738,7 @@ int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_
     int rc = check_launch("das_tc_pack_kernel");
     if (rc) return rc;
     const size_t smem = smem_bytes(NF, C, A, NE);
-    cudaFuncSetAttribute(das_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TIDAS_CUDA(cudaFuncSetAttribute(das_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(P.tc_tiles, FT);
     das_tc_kernel<<<grid, kThreads, smem, st>>>(packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf,
                                                 NF, C, img);

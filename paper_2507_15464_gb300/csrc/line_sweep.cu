@@ -662,8 +662,11 @@ int launch_line_sweep(const tidas_line_params& p, const float* rf, const float* 
     line_table_kernel<<<(L.D * L.N + 255) / 256, 256, 0, st>>>(L, T);
     int rc = check_launch("line_table_kernel");
     if (rc == TIDAS_OK) {
-        cudaFuncSetAttribute(line_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        rc = check_cuda(cudaFuncSetAttribute(line_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem),
+                        "cudaFuncSetAttribute(line_sweep_kernel)");
+    }
+    if (rc == TIDAS_OK) {
         line_sweep_kernel<<<n_scat, 32 * line::kSweepWarps, smem, st>>>(
             L, T, rf, lines, r_first, n_scat, eps, theta, e_loc, e_glob);
         rc = check_launch("line_sweep_kernel");
@@ -695,8 +698,8 @@ int launch_line_envelope(int n_rows, int n, const float* x, float* env, cudaStre
     const size_t smem = sizeof(float) * (((size_t)n + 1) & ~(size_t)1) + sizeof(float2) * (size_t)n;
     if (smem > 220 * 1024)
         return set_error(TIDAS_ERR_UNSUPPORTED, "line envelope: rows of %d points do not fit", n);
-    cudaFuncSetAttribute(line_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    TIDAS_CUDA(cudaFuncSetAttribute(line_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem));
     line_envelope_kernel<<<n_rows, 256, smem, st>>>(n, x, env);
     return check_launch("line_envelope_kernel");
 }
@@ -721,8 +724,11 @@ int launch_line_fixed(const tidas_line_params& p, const float* rf, int r_first, 
     line_table_kernel<<<(L.D * L.N + 255) / 256, 256, 0, st>>>(L, T);
     int rc = check_launch("line_table_kernel");
     if (rc == TIDAS_OK) {
-        cudaFuncSetAttribute(line_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        rc = check_cuda(cudaFuncSetAttribute(line_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem),
+                        "cudaFuncSetAttribute(line_fixed_kernel)");
+    }
+    if (rc == TIDAS_OK) {
         line_fixed_kernel<<<n_scat, 64, smem, st>>>(L, T, rf, r_first, s, eps, out);
         rc = check_launch("line_fixed_kernel");
     }

@@ -295,7 +295,7 @@ int launch_mlp_infer(const double* samples, int n, const float* lo4, const float
         enc.lo[k] = lo4[k];
         enc.hi[k] = hi4[k];
     }
-    cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    TIDAS_CUDA(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     const int ntiles = (n + kM - 1) / kM;
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
     mlp_infer_kernel<<<grid, 192, kSmem, st>>>(m[0], m[1], m[2], m[3], bias[0], bias[1], bias[2],

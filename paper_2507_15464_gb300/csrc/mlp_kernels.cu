@@ -1,8 +1,8 @@
 // Learned tiDAS kernel generator: exact PSF training targets, a tcgen05 BF16
 // GEMM with fused bias / ReLU epilogue, and the small kernels of MLP
 // training (Adam on FP32 master weights, ReLU backward, bias gradients,
-// transposes, mean-squared error) and inference (feature encoding,
-// spatially varying tiDAS with per-pixel kernels).
+// transposes, mean-squared error) and inference (feature encoding, kernel
+// fallback and scaling).
 #include "common.cuh"
 #include "sm103_primitives.cuh"
 
@@ -177,7 +177,7 @@ int launch_mlp_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N
     if (rc) return rc;
     rc = make_map_2d_bf16(&tb, B, N, K, BN);
     if (rc) return rc;
-    cudaFuncSetAttribute(mlp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    TIDAS_CUDA(cudaFuncSetAttribute(mlp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     dim3 grid((M + kM - 1) / kM, (N + BN - 1) / BN);
     mlp_gemm_kernel<<<grid, 128, kSmem, st>>>(ta, tb, M, N, K, BN, bias, relu, c32, c16, ldc);
     return check_launch("mlp_gemm_kernel");
@@ -403,45 +403,6 @@ __global__ void psf_batch_kernel(PsfArgs A, const double* __restrict__ samples, 
     if (norm && t == 0) norm[i] = (float)s;
 }
 
-// ----------------------------------------------- spatially varying tiDAS
-// y[f][z][x] = sum_t h[z][x][t] * r[f][z][x - t + c]: Eq. (2.13) with a
-// kernel per pixel.  One block per row; each thread keeps its pixel's
-// kernel in registers and walks the frames, reading the staged input line
-// from shared memory (consecutive lanes read consecutive words).
-constexpr int kVarMaxTaps = 64;
-__global__ void __launch_bounds__(512) tidas_varying_kernel(const float* __restrict__ kern, int ld,
-                                                            int taps, int nz, int nx,
-                                                            const float* __restrict__ in,
-                                                            float* __restrict__ out, int nf) {
-    extern __shared__ float line[];  // [nx + taps]
-    const int iz = blockIdx.x;
-    const int c = taps / 2, off = taps - 1 - c;
-    const int len = nx + taps - 1;
-    for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
-        const int ix = x0 + threadIdx.x;
-        float h[kVarMaxTaps];
-#pragma unroll
-        for (int t = 0; t < kVarMaxTaps; ++t)
-            h[t] = (ix < nx && t < taps) ? __ldg(kern + ((size_t)iz * nx + ix) * ld + t) : 0.f;
-        for (int f = 0; f < nf; ++f) {
-            __syncthreads();
-            const float* src = in + ((size_t)f * nz + iz) * nx;
-            for (int j = threadIdx.x; j < len; j += blockDim.x) {
-                const int x = j - off;
-                line[j] = (x >= 0 && x < nx) ? __ldg(src + x) : 0.f;
-            }
-            __syncthreads();
-            if (ix < nx) {
-                float y = 0.f;
-#pragma unroll
-                for (int t = 0; t < kVarMaxTaps; ++t)
-                    if (t < taps) y = fmaf(h[t], line[ix + taps - 1 - t], y);
-                out[((size_t)f * nz + iz) * nx + ix] = y;
-            }
-        }
-    }
-}
-
 // per-pixel NRMSE of learned vs exact kernels; where it exceeds `thresh` the
 // exact kernel replaces the learned one in `out`
 __global__ void kernel_fallback_kernel(const float* __restrict__ learned, int ldl,
@@ -637,23 +598,6 @@ extern "C" int tidas_encode(const double* samples, int32_t n, const float* lo4, 
     encode_kernel<<<(unsigned)(((long long)n * 8 + 255) / 256), 256, 0, ST(stream)>>>(
         samples, n, lo4, hi4, (__nv_bfloat16*)out16);
     return check_launch("encode_kernel");
-}
-
-extern "C" int tidas_forward_varying(const float* kernels, int32_t ld, int32_t taps, int32_t nz,
-                                     int32_t nx, const float* refl, float* img, int32_t n_frames,
-                                     void* stream) {
-    TIDAS_REQUIRE(kernels && refl && img, "tidas_forward_varying: null pointer");
-    TIDAS_REQUIRE(taps >= 1 && taps <= kVarMaxTaps && ld >= taps && nz >= 1 && nx >= 1 &&
-                      nx <= 16384 && n_frames >= 1,
-                  "tidas_forward_varying: bad sizes (taps <= %d)", kVarMaxTaps);
-    const int threads = nx < 512 ? ((nx + 31) / 32) * 32 : 512;
-    const size_t smem = (size_t)(nx + taps) * sizeof(float);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(tidas_varying_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    tidas_varying_kernel<<<nz, threads, smem, ST(stream)>>>(kernels, ld, taps, nz, nx, refl, img,
-                                                           n_frames);
-    return check_launch("tidas_varying_kernel");
 }
 
 extern "C" int tidas_kernel_fallback(const float* learned, int32_t ldl, const float* exact,

@@ -167,7 +167,7 @@ int launch_tidas_direct(const float* kern, int taps, int center, bool adjoint, i
     const bool fixed = W <= kWC;
     if (fixed) smem = (size_t)(tpad + 2 * kFB * kV * kWC) * sizeof(float);
     auto kernel = fixed ? tidas_direct_kernel<kWC> : tidas_direct_kernel<0>;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TIDAS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // forward: hr[s] = h[taps-1-s], off = taps-1-center; adjoint: hr = h, off = center
     const int off = adjoint ? center : taps - 1 - center;
     // rows x runs of frame groups: enough blocks for a few waves of 152 SMs
@@ -319,7 +319,7 @@ int launch_tidas_direct2d(const float* kern, int kz, int taps, bool adjoint, int
     if (nx % 4 == 0 && ((uintptr_t)out % 16) != 0)
         return set_error(TIDAS_ERR_ARG, "tidas 2D direct: output must be 16-byte aligned");
     auto kernel = fixed ? tidas_direct2d_kernel<kWC> : tidas_direct2d_kernel<0>;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TIDAS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // forward: taps reversed, off = taps-1-c; adjoint: taps as stored, off = c
     const int center = taps / 2;
     const int off = adjoint ? center : taps - 1 - center;

@@ -449,14 +449,14 @@ int launch_tidas_gemm(const float* kern, int taps, int center, bool adjoint, int
     const int grid = items < sm_count() ? items : sm_count();
     if (resid) {
         using C = gemm::Cfg<true>;
-        cudaFuncSetAttribute(tidas_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)C::kSmem);
+        TIDAS_CUDA(cudaFuncSetAttribute(tidas_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::kSmem));
         tidas_gemm_kernel<true><<<grid, C::kThreads, C::kSmem, st>>>(
             map_in, map_out, (const float*)in, kern, taps, center, adjoint ? 1 : 0, nz, nx, nf);
     } else {
         using C = gemm::Cfg<false>;
-        cudaFuncSetAttribute(tidas_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)C::kSmem);
+        TIDAS_CUDA(cudaFuncSetAttribute(tidas_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::kSmem));
         tidas_gemm_kernel<false><<<grid, C::kThreads, C::kSmem, st>>>(
             map_in, map_out, nullptr, kern, taps, center, adjoint ? 1 : 0, nz, nx, nf);
     }
@@ -854,20 +854,26 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
     }
     const int nm = (nf + gemm::kM - 1) / gemm::kM, nq = gemm2::n_chunks(nx);
     const size_t images = (size_t)nz * nm * nq;
-    if (images > (size_t)INT_MAX)
-        return set_error(TIDAS_ERR_UNSUPPORTED, "tidas 2D GEMM: %zu chunk images", images);
-    tidas_band_pack_kernel<<<(unsigned)images, 256, 0, st>>>((const __nv_bfloat16*)in, packed, nz,
-                                                             nx, nf, nm, nq);
-    rc = check_launch("tidas_band_pack_kernel");
+    if (images > (size_t)INT_MAX) {
+        rc = set_error(TIDAS_ERR_UNSUPPORTED, "tidas 2D GEMM: %zu chunk images", images);
+    } else {
+        tidas_band_pack_kernel<<<(unsigned)images, 256, 0, st>>>((const __nv_bfloat16*)in, packed,
+                                                                 nz, nx, nf, nm, nq);
+        rc = check_launch("tidas_band_pack_kernel");
+    }
     if (rc == TIDAS_OK) {
         const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
         const int items = nz * nm * ((ntiles + gemm::kTilesPerItem - 1) / gemm::kTilesPerItem);
         const int grid = items < sm_count() ? items : sm_count();
-        cudaFuncSetAttribute(tidas_gemm2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gemm2::kSmem);
-        tidas_gemm2d_kernel<<<grid, gemm2::kThreads, gemm2::kSmem, st>>>(
-            packed, map_out, kern, kz, taps, adjoint ? 1 : 0, nz, nx, nf);
-        rc = check_launch("tidas_gemm2d_kernel");
+        rc = check_cuda(cudaFuncSetAttribute(tidas_gemm2d_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm2::kSmem),
+                        "cudaFuncSetAttribute(tidas_gemm2d_kernel)");
+        if (rc == TIDAS_OK) {
+            tidas_gemm2d_kernel<<<grid, gemm2::kThreads, gemm2::kSmem, st>>>(
+                packed, map_out, kern, kz, taps, adjoint ? 1 : 0, nz, nx, nf);
+            rc = check_launch("tidas_gemm2d_kernel");
+        }
     }
     if (!workspace) cudaFreeAsync(packed, st);
     return rc;

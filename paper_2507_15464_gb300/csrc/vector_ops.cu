@@ -147,7 +147,10 @@ extern "C" int tidas_axpby(const float* a, const float* b, float* out, int64_t n
 // holds it until the process exits.  Host code cannot use the name of the
 // array as a device address, so the first call on each device looks the
 // address up with cudaGetSymbolAddress (with that device current) and keeps
-// it; make that first call before any stream capture.  All calls share the
+// it; make that first call before any stream capture.  The kept address is
+// the array's place in the module loaded into the device's context; a
+// cudaDeviceReset unloads that module, so it is not valid across a reset.
+// All calls share the
 // array and it keeps the previous call's contents; every partial this call
 // reads is written by the same call first, so nothing needs clearing.  Calls
 // that overlap on the GPU (for example on two streams) race on the array.

@@ -256,6 +256,33 @@ def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None, worksp
     return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out, workspace)
 
 
+def _varying(fn, kernels, x, variant, out=None):
+    if kernels.dim() == 3:
+        nz, nx, taps = kernels.shape
+        kz = 1
+    else:
+        nz, nx, kz, taps = kernels.shape
+    nf = x.shape[0]
+    _need(kernels, torch.float32, tuple(kernels.shape), "kernels")
+    _need(x, torch.float32, (nf, nz, nx), "input")
+    out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
+                                                  device=x.device)
+    fn(_ptr(kernels), taps, kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
+    return out
+
+
+def tidas_forward_varying(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
+    """Eq. (2.13) with a kernel per pixel (each pixel adds its own
+    single-scatterer image): kernels [nz, nx, taps] (row form) or
+    [nz, nx, kz, taps] (band form), refl [B, nz, nx] -> img [B, nz, nx]."""
+    return _varying(capi.tidas_forward_varying_2d, kernels, refl, variant, out)
+
+
+def tidas_adjoint_varying(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
+    """Transpose of tidas_forward_varying: img [B, nz, nx] -> refl [B, nz, nx]."""
+    return _varying(capi.tidas_adjoint_varying_2d, kernels, img, variant, out)
+
+
 class LineExperiment:
     """The single-line experiment of Section 3 on the GPU: channel data of a
     unit scatterer on every line point, DAS lines, and the sweep of Eq. (2.8)

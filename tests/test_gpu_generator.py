@@ -6,8 +6,11 @@ kernels of plain tiDAS on an unseen geometry.
 
 Tolerances: GEMM 1e-5 relative L2 (FP32 accumulation of exact BF16
 products); PSF rows 1e-5 (FP32 pulse evaluation, FP64 delays); MLP gradients
-3e-2 (the GPU rounds activations and gradients to BF16 between layers, unit
-roundoff 2^-8, while the reference stays in FP64).
+2e-3 against the FP64 oracle MLP with the GPU's BF16 rounding points applied
+between its layers (left over: FP32 against FP64 accumulation, and the rare
+BF16 rounding that this moves across a boundary, one ulp 2^-8); one AdamW
+step 1e-6 on the moments and weights against an FP64 step written from
+Loshchilov & Hutter (decoupled weight decay, bias-corrected moments).
 """
 import math
 
@@ -171,23 +174,71 @@ def test_psf_batch_matches_oracle():
         assert np.all(out[i, 63:] == 0)
 
 
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().double().numpy()
+
+
 def test_mlp_backward_matches_fp64_reference():
+    # the GPU rounds every hidden activation (after the ReLU) and every
+    # gradient that meets a weight matrix to BF16; the oracle MLP applies the
+    # same rounding points and otherwise stays in FP64
     from oracle import mlp as orc
     from paper_2507_15464_gb300.ops import DasPlan
     g = G()
     P = DasPlan(presets.geometry("pw128_compound"))
     s, tgt = g.training_set(P, n=256, seed=63)
-    net = g.KernelMLP(batch=256)
+    # non-zero biases so that every bias path carries a value
+    params = [(w, generators.uniform(b.shape, -0.1, 0.1, (67, l), np.float32))
+              for l, (w, b) in enumerate(g.init_params())]
+    net = g.KernelMLP(params, batch=256)
     x16 = torch.empty((256, 64), dtype=torch.bfloat16, device="cuda")
     net.encode(s, x16)
     net.train_step(x16, tgt, lr=0.0, wd=0.0)
     params = [(host(W16), host(b)) for W16, b in zip(net.W16, net.b)]
-    acts = orc.forward(params, host(x16))
-    grads = orc.backward(params, acts, host(tgt), 63)
-    assert float(net.loss) == pytest.approx(orc.mse(acts[-1], host(tgt), 63), rel=3e-2)
+    acts = orc.forward(params, host(x16), act_round=_bf16)
+    grads = orc.backward(params, acts, host(tgt), 63, grad_round=_bf16)
+    assert float(net.loss) == pytest.approx(orc.mse(acts[-1], host(tgt), 63), rel=1e-4)
     for l in range(4):
-        assert rel_l2(host(net.gW[l]), grads[l][0]) <= 3e-2, l
-        assert rel_l2(host(net.gb[l]), grads[l][1]) <= 3e-2, l
+        assert rel_l2(host(net.gW[l]), grads[l][0]) <= 2e-3, l
+        assert rel_l2(host(net.gb[l]), grads[l][1]) <= 2e-3, l
+    # the exact FP64 chain rule differs from the GPU by the BF16 roundings
+    # (a few 1e-3), which is why the rounding points are applied above
+    exact = orc.backward(params, orc.forward(params, host(x16)), host(tgt), 63)
+    assert rel_l2(host(net.gW[0]), exact[0][0]) <= 5e-2
+
+
+def test_adamw_step_matches_loshchilov_hutter():
+    # one AdamW step (Loshchilov & Hutter, "Decoupled weight decay
+    # regularization"): m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+    # m^ = m / (1 - b1^t), v^ = v / (1 - b2^t),
+    # w <- w - lr (m^ / (sqrt(v^) + eps) + wd w), in FP64
+    from paper_2507_15464_gb300 import capi
+    from paper_2507_15464_gb300.ops import _ptr, _stream
+    rows, cols, step = 37, 70, 3
+    lr, b1, b2, eps, wd = 1e-3, 0.9, 0.999, 1e-8, 1e-2
+    w = generators.standard_normal((rows, cols), (80, 0), np.float32)
+    m = 0.1 * generators.standard_normal((rows, cols), (80, 1), np.float32)
+    v = 0.01 * np.abs(generators.standard_normal((rows, cols), (80, 2), np.float32))
+    gr = generators.standard_normal((rows, cols), (80, 3), np.float32)
+    wd_, md, vd, gd = (to_dev(a) for a in (w, m, v, gr))
+    w16 = torch.empty((rows, cols), dtype=torch.bfloat16, device="cuda")
+    w16t = torch.empty((cols, rows), dtype=torch.bfloat16, device="cuda")
+    capi.call("tidas_adam", _ptr(wd_), _ptr(md), _ptr(vd), _ptr(gd), rows, cols, lr, b1, b2, eps,
+              wd, step, _ptr(w16), _ptr(w16t), _stream())
+    W, M, V, Gr = (a.astype(np.float64) for a in (w, m, v, gr))
+    m1 = b1 * M + (1 - b1) * Gr
+    v1 = b2 * V + (1 - b2) * Gr * Gr
+    mh, vh = m1 / (1 - b1 ** step), v1 / (1 - b2 ** step)
+    w1 = W - lr * (mh / (np.sqrt(vh) + eps) + wd * W)
+    assert rel_l2(host(md), m1) <= 1e-6
+    assert rel_l2(host(vd), v1) <= 1e-6
+    assert rel_l2(host(wd_), w1) <= 1e-6
+    # the update itself (a 1e-3 change of an O(1) weight, so FP32 rounding of
+    # the weight leaves ~1e-4 of it)
+    assert rel_l2(host(wd_) - W, w1 - W) <= 5e-4
+    # the BF16 copies are the rounded new weights and their transpose
+    np.testing.assert_array_equal(host(w16), _bf16(host(wd_)))
+    np.testing.assert_array_equal(host(w16t), _bf16(host(wd_)).T)
 
 
 def _perms(epochs, n, seed):
@@ -221,7 +272,7 @@ def test_learned_kernels_beat_shift_invariant_kernels_on_unseen_geometry():
     net = g.KernelMLP(batch=256)
     x16 = torch.empty((20000, 64), dtype=torch.bfloat16, device="cuda")
     net.encode(s, x16)
-    net.fit(x16, tgt, 60, _perms(60, 20000, 5), lr0=1e-3)
+    net.fit(x16, tgt, 100, _perms(100, 20000, 5), lr0=1e-3)
     fnum, ang = 1.7, 7.5 * math.pi / 180.0          # not a training draw
     sub = dict(geom, nz=64, z0=geom["z0"] + 400 * geom["dz"])  # 64 rows x 512 columns
     smp = g.grid_samples(sub, fnum, ang)
@@ -240,6 +291,11 @@ def test_learned_kernels_beat_shift_invariant_kernels_on_unseen_geometry():
     err_mixed = np.linalg.norm(host(mixed)[:, :63] - ex[:, :63], axis=1) / \
         np.linalg.norm(ex[:, :63], axis=1)
     assert err_mixed.max() <= 0.02 + 1e-6
-    assert err_mixed.mean() < err_si.mean()
-    fallback = float((host(err_l) > 0.02).mean())
-    assert fallback < 1.0  # the network serves part of the grid on its own
+    # the network's own kernels, before any fallback: on average and on most
+    # pixels closer to the exact kernels than the shift-invariant ones, and
+    # good enough (NRMSE <= 2 %) to serve most of the grid without fallback
+    e_l = host(err_l)
+    assert e_l.mean() < 0.5 * err_si.mean(), (e_l.mean(), err_si.mean())
+    assert float((e_l < err_si).mean()) > 0.5
+    fallback = float((e_l > 0.02).mean())
+    assert fallback < 0.5, fallback
