@@ -12,6 +12,12 @@ L2, so every step streams it from HBM).  tiDAS is timed on 256 frames of
 geometry.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+python bench.py --profile-case CASE [--frames F] [--dtype f16|f32] [--variant V]
+                [--kz KZ] [--kernels N] [--iters I]
+
+--profile-case runs one kernel case a few times on seeded random inputs of
+the benchmark's shapes and prints nothing but "ok": the command that the
+profiler summaries run under ncu.  Nothing is timed or checked there.
 """
 import argparse
 import json
@@ -44,9 +50,89 @@ def parse():
     ap.add_argument("--no-fista", action="store_true")
     ap.add_argument("--no-line", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-config1", action="store_true")
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--fista-iters", type=int, default=200)
+    ap.add_argument("--profile-case", default=None,
+                    choices=["das", "das_adjoint", "tidas", "tidas_adjoint", "tidas2d",
+                             "tidas2d_adjoint", "varying", "line", "mlp"])
+    ap.add_argument("--frames", type=int, default=8)
+    ap.add_argument("--dtype", default="f16", choices=["f16", "f32"])
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--kz", type=int, default=16)
+    ap.add_argument("--geom", default=GEOM)
+    ap.add_argument("--kernels", type=int, default=524288)
     return ap.parse_args()
+
+
+def run_profile_case(a):
+    """One kernel case, a.iters times, on seeded random inputs (the kernels'
+    cost does not depend on the values)."""
+    import torch
+    from paper_2507_15464_gb300 import ops
+    from tidas_workloads import presets
+    g = presets.geometry(a.geom)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    if a.profile_case == "mlp":
+        # fused inference of the kernel generator (untrained weights): samples
+        # uniform over its (x, z, F#, angle) domain
+        from paper_2507_15464_gb300 import generator
+        P = ops.DasPlan(g)
+        net = generator.KernelMLP()
+        lo = torch.tensor(generator.BOUNDS_LO, dtype=torch.float64, device="cuda")
+        hi = torch.tensor(generator.BOUNDS_HI, dtype=torch.float64, device="cuda")
+        u = torch.rand((a.kernels, 4), dtype=torch.float64, device="cuda", generator=gen)
+        s = lo + u * (hi - lo)
+        fn = lambda: net.infer(P, s)
+    elif a.profile_case == "line":
+        # the single-line experiment: 600 points, 192 elements, focus 25 mm
+        p = dict(n_elem=192, pitch=0.3e-3, f0=5e6, fs=40e6, c=1540.0, frac_bw=0.6,
+                 n_samples=2560, n_depths=600, z_first=2e-3, z_last=42e-3, z_focus=25e-3,
+                 kossoff=0.6, fnum_rx=1.0, interp=1)
+        E = ops.LineExperiment(p)
+        eps = E.window()
+        rf = E.synthesize()
+        lines = E.das_lines(rf)
+
+        def fn():
+            E.synthesize(out=rf)
+            E.das_lines(rf, out=lines)
+            E.sweep(rf, lines, eps)
+    elif a.profile_case in ("das", "das_adjoint"):
+        dt = torch.float16 if (a.dtype == "f16" and a.profile_case == "das") else torch.float32
+        P = ops.DasPlan(g, rf_dtype=dt)
+        if a.profile_case == "das":
+            x = torch.randn(P.rf_shape(a.frames), device="cuda", generator=gen).to(dt)
+            fn = lambda: P.forward(x)
+        else:
+            x = torch.randn(P.img_shape(a.frames), device="cuda", generator=gen)
+            fn = lambda: P.adjoint(x)
+    elif a.profile_case == "varying":
+        # per-pixel kernels (row form at kz = 1, band form above)
+        nz, nx = g["nz"], g["nx"]
+        shape = (nz, nx, TAPS) if a.kz == 1 else (nz, nx, a.kz, TAPS)
+        k = torch.randn(shape, device="cuda", generator=gen)
+        x = torch.randn((a.frames, nz, nx), device="cuda", generator=gen)
+        if a.variant == 1:
+            x = x.to(torch.bfloat16)
+        fn = lambda: ops.tidas_forward_varying(k, x, variant=a.variant)
+    else:
+        nz, nx = g["nz"], g["nx"]
+        band = a.profile_case.startswith("tidas2d")
+        k = torch.randn((nz, a.kz, TAPS) if band else (nz, TAPS), device="cuda", generator=gen)
+        x = torch.randn((a.frames, nz, nx), device="cuda", generator=gen)
+        if a.variant == 1:
+            x = x.to(torch.bfloat16)
+        if band:
+            f = ops.tidas_forward_2d if a.profile_case == "tidas2d" else ops.tidas_adjoint_2d
+        else:
+            f = ops.tidas_forward if a.profile_case == "tidas" else ops.tidas_adjoint
+        fn = lambda: f(k, x, variant=a.variant)
+    for _ in range(a.iters):
+        fn()
+    torch.cuda.synchronize()
+    print("ok")
 
 
 def dist_env():
@@ -349,6 +435,11 @@ def run_ours(args):
            "serial": {"value": whole_job_mpix_s(BATCH, npx, world, serial_ms),
                       "ms_per_step": serial_ms}}
 
+    # ---- the 64-element single-angle case (DAS, 31-tap fit and apply)
+    if rank == 0 and not args.no_config1:
+        extra["config1"] = bench_config1(torch, ops, capi, generators, stream, args,
+                                         cpu=not args.no_cpu_baseline)
+
     # ---- tiDAS variants on the 256-frame reflectivity batch
     if not args.no_tidas:
         extra["tidas"] = bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak,
@@ -512,8 +603,14 @@ def bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, das0, args, stream,
              "speedup_vs_das_per_frame": das_ms_per_frame / (m / nf)}
         if variant == capi.VARIANT_GEMM_BF16:
             a = mma / (m * 1e-3) / 1e12
-            # the call is the operand repack plus the GEMM; both are in `ms`
-            r["tensor"] = {"mma_tflops": a, "peak_tflops": bf16_peak, "frac": a / bf16_peak,
+            u = useful / (m * 1e-3) / 1e12
+            # the call is the operand repack plus the GEMM; both are in `ms`.
+            # frac counts the method's own work (2 kz taps flop per output
+            # pixel); the executed MMA work also multiplies the zero band
+            # padding (K = 192 columns per 128-column tile for 63 taps)
+            r["tensor"] = {"useful_tflops": u, "peak_tflops": bf16_peak, "frac": u / bf16_peak,
+                           "useful_flops_per_call": useful,
+                           "mma_tflops": a, "mma_frac": a / bf16_peak,
                            "mma_flops_per_call": mma, "timed": "repack + GEMM"}
         rows = [0, 333, nz - 1]
         frames = np.array([0, nf - 1])
@@ -772,6 +869,108 @@ def bench_fista(torch, capi, generators, iters, cpu=True):
         res["oracle_cpu_tidas"] = {"kind": "oracle", "iters": n_it, "ms_per_iter": dt / n_it * 1e3,
                                    "cores": int(os.environ.get("OMP_NUM_THREADS",
                                                                os.cpu_count() or 1))}
+        res["oracle_cpu_exact"] = oracle_exact_iteration_estimate(g, x_true[0].cpu().numpy())
+    return res
+
+
+def oracle_exact_iteration_estimate(g, x_true, frac=64):
+    """One FISTA iteration with the exact operator costs a synthesis of the
+    whole grid, a DAS of the whole grid and their transposes (the same loops
+    as the forward maps).  The FP64 oracle's cost is linear in the pixels it
+    synthesises and beamforms, so it is timed on 1/frac of them (pixels with
+    a stride of frac through the grid, every one synthesised with its own
+    reflectivity, and the DAS of as many pixels) and scaled to the grid:
+    iteration ~ 2 (synthesis + DAS)."""
+    import oracle
+    O = oracle.Oracle(g)
+    npx = g["nx"] * g["nz"]
+    sel = np.arange(0, npx, frac)
+    pos = O.grid_positions()[sel]
+    amp = np.zeros((sel.size, 2))
+    amp[:, 0] = x_true.ravel()[sel]
+    amp[amp[:, 0] == 0, 0] = 1.0  # every sampled pixel costs a full synthesis
+    t0 = time.perf_counter()
+    rf = O.synthesize(pos, amp)
+    t1 = time.perf_counter()
+    O.das_pixels(rf, sel)
+    t2 = time.perf_counter()
+    synth_s, das_s = (t1 - t0) * frac, (t2 - t1) * frac
+    return {"kind": "oracle", "ms_per_iter": 2.0 * (synth_s + das_s) * 1e3,
+            "synthesis_s": synth_s, "das_s": das_s,
+            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+            "sample": "synthesis and DAS of 1/%d of the 1024 x 1024 pixels, scaled to the "
+                      "grid; an iteration counts each map and its transpose" % frac}
+
+
+def bench_config1(torch, ops, capi, generators, stream, args, cpu=True):
+    """The 64-element case: one 0 degree plane wave, 2048 x 64 FP32 channel
+    data from 200 N(0,1) scatterers in a 19 x 30 mm box (seed 0), a 128 x 256
+    image with linear interpolation and F# 1.5 Hann apodization; 31-tap row
+    kernels fitted from exact single-scatterer PSFs and applied to the same
+    scatterers placed on their nearest pixels."""
+    import oracle
+    from tidas_workloads import presets
+    g = presets.geometry("pw64_single")
+    P = ops.DasPlan(g)
+    pos, amp = generators.single_frame_speckle(0, n=200)
+    posd = torch.from_numpy(np.ascontiguousarray(pos[None])).cuda()
+    ampd = torch.from_numpy(np.ascontiguousarray(amp[None]).astype(np.float32)).cuda()
+    rf = P.synthesize(posd, ampd)
+    img = torch.empty(P.img_shape(1), device="cuda")
+    npx = g["nx"] * g["nz"]
+    res = {"workload": "64 el, 0 deg, 2048 samples, 128 x 256 px, linear, F# 1.5, FP32",
+           "scatterers": 200}
+    ms_syn = time_steps(torch, lambda: P.synthesize(posd, ampd, out=rf), max(3, args.steps), 2,
+                        stream)
+    ms = time_steps(torch, lambda: P.forward(rf, out=img), max(3, args.steps), 2, stream)
+    O = oracle.Oracle(g)
+    rf_h = rf[0].double().cpu().numpy()
+    t0 = time.perf_counter()
+    ref = O.das(rf_h)
+    t_orc = time.perf_counter() - t0
+    got = img[0].double().cpu().numpy()
+    res["das"] = {"ms": ms, "mpix_s": npx / (ms * 1e-3) / 1e6, "synthesis_ms": ms_syn,
+                  "nrmse_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    # tiDAS: 31-tap kernels, the scatterers on their nearest pixels
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    k31, _ = P.fit_kernels(31)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    refl = np.zeros((1, g["nz"], g["nx"]), np.float32)
+    ix = np.clip(np.floor((pos[:, 0] - g["x0"]) / g["dx"]).astype(int), 0, g["nx"] - 1)
+    iz = np.clip(np.floor((pos[:, 1] - g["z0"]) / g["dz"]).astype(int), 0, g["nz"] - 1)
+    np.add.at(refl[0], (iz, ix), amp[:, 0].astype(np.float32))
+    refl_d = torch.from_numpy(refl).cuda()
+    exact = P.forward(P.synthesize_grid(refl_d))
+    kh = k31.double().cpu().numpy()
+    tref = oracle.tidas_conv(kh, refl.astype(np.float64))
+    res["tidas"] = {"taps": 31, "fit_ms": t0e.elapsed_time(t1e)}
+    for variant, name in ((capi.VARIANT_DIRECT, "direct_f32"), (capi.VARIANT_GEMM_BF16, "gemm_bf16"),
+                          (capi.VARIANT_GEMM_RESID, "gemm_resid")):
+        x = refl_d.to(torch.bfloat16) if variant == capi.VARIANT_GEMM_BF16 else refl_d
+        out = torch.empty_like(refl_d)
+        m = time_steps(torch, lambda: ops.tidas_forward(k31, x, variant=variant, out=out),
+                       max(3, args.steps), 2, stream)
+        y = out[0].double()
+        res["tidas"][name] = {
+            "ms": m, "mpix_s": npx / (m * 1e-3) / 1e6,
+            "nrmse_vs_oracle": float(np.linalg.norm(y.cpu().numpy() - tref) / np.linalg.norm(tref)),
+            "nrmse_vs_exact_das": float((y - exact[0].double()).norm() / exact[0].double().norm()),
+            "speedup_vs_das": ms / m}
+    if cpu:
+        t0 = time.perf_counter()
+        kf, _ = O.fit_kernels(31)
+        t_fit = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.tidas_conv(kf, refl.astype(np.float64))
+        t_conv = time.perf_counter() - t0
+        res["oracle_cpu"] = {"kind": "oracle",
+                             "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                             "das_mpix_s": npx / t_orc / 1e6, "das_ms": t_orc * 1e3,
+                             "tidas_fit_ms": t_fit * 1e3, "tidas_conv_ms": t_conv * 1e3,
+                             "tidas_mpix_s": npx / t_conv / 1e6}
+    P.close()
     return res
 
 
@@ -894,7 +1093,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile_case:
+        run_profile_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -467,6 +467,21 @@ const char* tidas_last_error(void);
  * otherwise a code naming the wait.  Returns TIDAS_ERR_TIMEOUT when set. */
 int tidas_device_status(int32_t* status);
 
+/* Failure-path test hooks (the paper has no counterpart).  They exist so that
+ * a test can make a bounded device wait run out without faulting or hanging
+ * the GPU, and check that the flag reaches tidas_device_status.  Both apply
+ * to tidas_gemm_bf16 launches made after the call, process-wide:
+ *   TIDAS_DEBUG_WAIT_LIMIT_NS  limit of that kernel's bounded waits, in ns
+ *                              (default 1e9; 1e3 <= value <= 1e10)
+ *   TIDAS_DEBUG_SKIP_COPIES    1: its producer issues no copies, so its MMA
+ *                              thread's first wait runs out (code 202) with
+ *                              nothing in flight and the output is left
+ *                              unwritten; 0 (default): normal operation
+ * Unknown options and out-of-range values return TIDAS_ERR_ARG. */
+#define TIDAS_DEBUG_WAIT_LIMIT_NS 1
+#define TIDAS_DEBUG_SKIP_COPIES 2
+int tidas_set_debug_option(int32_t option, int64_t value);
+
 #ifdef __cplusplus
 }
 #endif

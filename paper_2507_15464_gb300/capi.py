@@ -13,6 +13,7 @@ TIDAS_OK, TIDAS_ERR_ARG, TIDAS_ERR_CUDA, TIDAS_ERR_TIMEOUT, TIDAS_ERR_UNSUPPORTE
 RF_F32, RF_F16 = 0, 1
 INTERP_LINEAR, INTERP_CUBIC = 0, 1
 VARIANT_DIRECT, VARIANT_GEMM_BF16, VARIANT_GEMM_RESID = 0, 1, 2
+DEBUG_WAIT_LIMIT_NS, DEBUG_SKIP_COPIES = 1, 2
 
 
 class TidasError(RuntimeError):
@@ -63,6 +64,7 @@ _SIG = {
     "tidas_forward": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_adjoint": [_P, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_device_status": [ctypes.POINTER(ctypes.c_int32)],
+    "tidas_set_debug_option": [_I, ctypes.c_int64],
     "tidas_dot": [_P, _P, ctypes.c_int64, _P, _P],
     "tidas_dot_noalloc": [_P, _P, ctypes.c_int64, _P, _P],
     "tidas_asum": [_P, ctypes.c_int64, _P, _P],
@@ -285,3 +287,7 @@ def tidas_device_status():
 
 def tidas_last_error():
     return load().tidas_last_error().decode(errors="replace")
+
+
+def tidas_set_debug_option(option, value):
+    return _check(load().tidas_set_debug_option(option, value))

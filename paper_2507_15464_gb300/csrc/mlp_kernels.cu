@@ -3,6 +3,8 @@
 // training (Adam on FP32 master weights, ReLU backward, bias gradients,
 // transposes, mean-squared error) and inference (feature encoding, kernel
 // fallback and scaling).
+#include <atomic>
+
 #include "common.cuh"
 #include "sm103_primitives.cuh"
 
@@ -29,10 +31,14 @@ constexpr int kBBytes = kMaxBN * kKC * 2;  // 32 KB (max)
 constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 }  // namespace mg
 
+// skip_loads (failure-path tests only): the producer issues no copies, so the
+// MMA thread's first wait runs out after wait_ns with nothing in flight,
+// records code 202 and the CTA returns without writing its tile.
 __global__ void __launch_bounds__(128, 1)
     mlp_gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                     int M, int N, int K, int BN, const float* __restrict__ bias, int relu,
-                    float* __restrict__ c32, __nv_bfloat16* __restrict__ c16, int ldc) {
+                    float* __restrict__ c32, __nv_bfloat16* __restrict__ c16, int ldc,
+                    int skip_loads, unsigned long long wait_ns) {
     using namespace mg;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -71,10 +77,10 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0 && lane == 0 && !skip_loads) {
         uint32_t st = 0, ph = 0;
         for (int kc = 0; kc < nk; ++kc) {
-            if (!mbar_wait(&empty[st], ph ^ 1, &g_mlp_wait_error, 201)) {
+            if (!mbar_wait(&empty[st], ph ^ 1, &g_mlp_wait_error, 201, wait_ns)) {
                 *s_abort = 1;
                 break;
             }
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(128, 1)
     } else if (warp == 1 && lane == 0) {
         uint32_t st = 0, ph = 0;
         for (int kc = 0; kc < nk; ++kc) {
-            if (*s_abort || !mbar_wait(&full[st], ph, &g_mlp_wait_error, 202)) {
+            if (*s_abort || !mbar_wait(&full[st], ph, &g_mlp_wait_error, 202, wait_ns)) {
                 *s_abort = 1;
                 break;
             }
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(done);
     }
     __syncwarp();
-    if (!mbar_wait(done, 0, &g_mlp_wait_error, 203)) *s_abort = 1;
+    if (!mbar_wait(done, 0, &g_mlp_wait_error, 203, wait_ns)) *s_abort = 1;
     tc_fence_after();
     if (!*s_abort) {
         const int row = m0 + warp * 32 + lane;
@@ -167,6 +173,11 @@ int read_clear_mlp_wait_flag(int* v) {
 
 int make_map_2d_bf16(CUtensorMap* map, const void* ptr, int rows, int cols, int box_rows);
 
+// Failure-path test hooks of the GEMM (tidas_set_debug_option), read by the
+// host when it launches the kernel.
+static std::atomic<int> g_dbg_skip_loads{0};
+static std::atomic<unsigned long long> g_dbg_wait_ns{1000000000ull};
+
 int launch_mlp_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K,
                     const float* bias, int relu, float* c32, __nv_bfloat16* c16, int ldc,
                     cudaStream_t st) {
@@ -179,7 +190,8 @@ int launch_mlp_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N
     if (rc) return rc;
     TIDAS_CUDA(cudaFuncSetAttribute(mlp_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     dim3 grid((M + kM - 1) / kM, (N + BN - 1) / BN);
-    mlp_gemm_kernel<<<grid, 128, kSmem, st>>>(ta, tb, M, N, K, BN, bias, relu, c32, c16, ldc);
+    mlp_gemm_kernel<<<grid, 128, kSmem, st>>>(ta, tb, M, N, K, BN, bias, relu, c32, c16, ldc,
+                                              g_dbg_skip_loads.load(), g_dbg_wait_ns.load());
     return check_launch("mlp_gemm_kernel");
 }
 
@@ -618,4 +630,21 @@ extern "C" int tidas_row_scale(const float* in, int32_t ldi, const float* s, int
     row_scale_kernel<<<(int)((rows + 7) / 8), dim3(32, 8), 0, ST(stream)>>>(in, ldi, s, rows, cols,
                                                                            out, ldo);
     return check_launch("row_scale_kernel");
+}
+
+extern "C" int tidas_set_debug_option(int32_t option, int64_t value) {
+    switch (option) {
+        case TIDAS_DEBUG_WAIT_LIMIT_NS:
+            TIDAS_REQUIRE(value >= 1000 && value <= 10000000000ll,
+                          "tidas_set_debug_option: wait limit %lld ns outside [1e3, 1e10]",
+                          (long long)value);
+            g_dbg_wait_ns.store((unsigned long long)value);
+            return TIDAS_OK;
+        case TIDAS_DEBUG_SKIP_COPIES:
+            TIDAS_REQUIRE(value == 0 || value == 1, "tidas_set_debug_option: skip must be 0 or 1");
+            g_dbg_skip_loads.store((int)value);
+            return TIDAS_OK;
+        default:
+            return set_error(TIDAS_ERR_ARG, "tidas_set_debug_option: unknown option %d", option);
+    }
 }

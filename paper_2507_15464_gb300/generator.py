@@ -176,16 +176,20 @@ class KernelMLP:
             capi.call("tidas_adam", _ptr(self.b[l]), _ptr(self.mb[l]), _ptr(self.vb[l]),
                       _ptr(self.gb[l]), 1, o, lr, 0.9, 0.999, 1e-8, 0.0, t, None, None, st)
 
-    def fit(self, x16_all, targets_all, epochs, perms, lr0=1e-3, log_every=0):
-        """Mini-batch AdamW over the whole set for `epochs` epochs with the given
-        per-epoch permutations (int32 [epochs, n], an input), cosine schedule."""
+    def fit(self, x16_all, targets_all, epochs, perms, lr0=1e-3, log_every=0, first_epoch=0,
+            total_epochs=None):
+        """Mini-batch AdamW over the whole set for epochs first_epoch ..
+        epochs - 1 of a run of total_epochs (default: epochs) with the given
+        per-epoch permutations (int32 [>= epochs, n], an input), cosine
+        schedule over the whole run.  first_epoch > 0 resumes a run restored
+        by load_checkpoint."""
         n = x16_all.shape[0]
         steps_per_epoch = n // self.B
-        total = epochs * steps_per_epoch
+        total = (total_epochs or epochs) * steps_per_epoch
         xb, tb = _bf16((self.B, IN)), _f32((self.B, OUT))
         losses = []
-        k = 0
-        for e in range(epochs):
+        k = first_epoch * steps_per_epoch
+        for e in range(first_epoch, epochs):
             perm = perms[e]
             for s in range(steps_per_epoch):
                 idx = perm[s * self.B:(s + 1) * self.B]
@@ -199,6 +203,32 @@ class KernelMLP:
             if log_every and (e % log_every == 0 or e == epochs - 1):
                 losses.append((e, float(self.loss)))
         return losses
+
+    # ------------------------------------------------------- checkpoint / resume
+    def save_checkpoint(self, path):
+        """Write the FP32 master weights and biases, the Adam moments and the
+        step count to an .npz file: all the state a resumed run needs (the
+        BF16 copies are rebuilt from the masters on load)."""
+        arrays = {"step": np.array(self.step_count, np.int64)}
+        for l in range(len(self.W)):
+            for name, lst in (("W", self.W), ("b", self.b), ("mW", self.mW), ("vW", self.vW),
+                              ("mb", self.mb), ("vb", self.vb)):
+                arrays["%s%d" % (name, l)] = lst[l].cpu().numpy()
+        np.savez(path, **arrays)
+
+    @classmethod
+    def load_checkpoint(cls, path, batch=256):
+        """A network restored from save_checkpoint: masters, moments and step
+        count as saved, BF16 copies rebuilt."""
+        with np.load(path) as z:
+            nl = len(LAYERS)
+            params = [(z["W%d" % l], z["b%d" % l]) for l in range(nl)]
+            net = cls(params, batch=batch)
+            for l in range(nl):
+                for name, lst in (("mW", net.mW), ("vW", net.vW), ("mb", net.mb), ("vb", net.vb)):
+                    lst[l].copy_(torch.from_numpy(z["%s%d" % (name, l)]))
+            net.step_count = int(z["step"])
+        return net
 
     # -------------------------------------------------------------- inference
     def infer(self, plan, samples, chunk=None):

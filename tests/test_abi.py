@@ -172,3 +172,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(capi._build, "LIB", str(tmp_path / "libtidas.so"))
     with pytest.raises(OSError, match="not been built"):
         capi.load(build_if_missing=False)
+
+
+def test_debug_options_are_validated_on_the_host():
+    # the failure-path test hooks reject unknown options and values outside
+    # their ranges before touching any device
+    for opt, val in ((capi.DEBUG_WAIT_LIMIT_NS, 10), (capi.DEBUG_WAIT_LIMIT_NS, 10 ** 11),
+                     (capi.DEBUG_SKIP_COPIES, 2), (99, 0)):
+        with pytest.raises(capi.TidasError) as e:
+            capi.tidas_set_debug_option(opt, val)
+        assert e.value.code == capi.TIDAS_ERR_ARG

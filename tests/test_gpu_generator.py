@@ -226,6 +226,9 @@ def test_adamw_step_matches_loshchilov_hutter():
     capi.call("tidas_adam", _ptr(wd_), _ptr(md), _ptr(vd), _ptr(gd), rows, cols, lr, b1, b2, eps,
               wd, step, _ptr(w16), _ptr(w16t), _stream())
     W, M, V, Gr = (a.astype(np.float64) for a in (w, m, v, gr))
+    # the ABI takes the hyperparameters as float: the reference uses those
+    # values (0.999 as float differs from 0.999 by 1.3e-8, i.e. 1.3e-5 of 1 - b2)
+    lr, b1, b2, eps, wd = (float(np.float32(h)) for h in (lr, b1, b2, eps, wd))
     m1 = b1 * M + (1 - b1) * Gr
     v1 = b2 * V + (1 - b2) * Gr * Gr
     mh, vh = m1 / (1 - b1 ** step), v1 / (1 - b2 ** step)
@@ -299,3 +302,35 @@ def test_learned_kernels_beat_shift_invariant_kernels_on_unseen_geometry():
     assert float((e_l < err_si).mean()) > 0.5
     fallback = float((e_l > 0.02).mean())
     assert fallback < 0.5, fallback
+
+
+def test_checkpoint_resume_matches_an_uninterrupted_run(tmp_path):
+    # 4 epochs straight, against 2 epochs, a checkpoint written to disk, a
+    # fresh network restored from it, and the last 2 epochs of the same
+    # schedule: every kernel of a training step has a fixed summation order,
+    # so the two runs end with bit-identical masters, moments and step count
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = G()
+    P = DasPlan(presets.geometry("pw128_compound"))
+    s, tgt = g.training_set(P, n=2048, seed=81)
+    x16 = torch.empty((2048, 64), dtype=torch.bfloat16, device="cuda")
+    g.KernelMLP(batch=256).encode(s, x16)
+    perms = _perms(4, 2048, 82)
+    a = g.KernelMLP(batch=256)
+    a.fit(x16, tgt, 4, perms, lr0=1e-3)
+    b = g.KernelMLP(batch=256)
+    b.fit(x16, tgt, 2, perms, lr0=1e-3, total_epochs=4)
+    path = tmp_path / "mlp.npz"
+    b.save_checkpoint(path)
+    del b
+    c = g.KernelMLP.load_checkpoint(path, batch=256)
+    assert c.step_count == 2 * (2048 // 256)
+    c.fit(x16, tgt, 4, perms, lr0=1e-3, first_epoch=2, total_epochs=4)
+    assert c.step_count == a.step_count
+    for l in range(4):
+        for x, y in ((a.W[l], c.W[l]), (a.b[l], c.b[l]), (a.mW[l], c.mW[l]), (a.vW[l], c.vW[l]),
+                     (a.W16[l], c.W16[l])):
+            assert torch.equal(x, y), l
+    # and the restored network infers like the original
+    smp = torch.from_numpy(np.array([[1e-3, 20e-3, 1.5, 0.05], [-5e-3, 40e-3, 2.5, -0.1]])).cuda()
+    assert torch.equal(a.infer(P, smp), c.infer(P, smp))
