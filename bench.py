@@ -536,6 +536,8 @@ def bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak, bf
     res["nrmse_vs_exact_das"] = float((out[0].double() - d).norm() / d.norm())
     res["band_2d"] = bench_tidas2d(torch, ops, capi, P32, refl, refl_bf, out, d, args, stream,
                                    bf16_peak, das_ms_per_frame)
+    res["frontier"] = bench_kz_frontier(torch, ops, capi, P32, refl, refl_bf, out, d, args,
+                                        stream, das_ms_per_frame)
     if not args.no_cpu_baseline:
         # the FP64 oracle's Eq. (2.13) on 8 of the frames, all rows, host cores
         import oracle
@@ -550,6 +552,38 @@ def bench_tidas(torch, ops, capi, generators, g, P16, args, stream, hbm_peak, bf
                              "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
                              "sample": "%d of the %d frames, every row, FP64" % (nfr, TIDAS_FRAMES)}
     return res
+
+
+def bench_kz_frontier(torch, ops, capi, P32, refl, refl_bf, out, das0, args, stream,
+                      das_ms_per_frame, kzs=(1, 4, 8, 16, 32)):
+    """Accuracy against speed of tiDAS over the band depth kz (63 taps) on the
+    same 256-frame batch: for each kz the kernels are fitted from the exact
+    PSFs, the tcgen05 band GEMM is timed, and its image is compared with the
+    FP64 oracle (sampled rows) and with exact DAS of the same reflectivity
+    (frame 0, FP32 direct form); the speed-up is per frame over the
+    tensor-core DAS of the headline step.  kz = 1 is the row-wise model."""
+    nf, nz, nx = refl.shape
+    rows = [0, 333, nz - 1]
+    frames = np.array([0, nf - 1])
+    xin = refl_bf[frames].double().cpu().numpy()
+    front = []
+    for kz in kzs:
+        kk = P32.fit_kernels_2d(kz, TAPS)
+        ws = ops.band_workspace(nz, nx, nf, capi.VARIANT_GEMM_BF16)
+        fn = lambda: ops.tidas_forward_2d(kk, refl_bf, variant=capi.VARIANT_GEMM_BF16,  # noqa: E731
+                                          out=out, workspace=ws)
+        m = time_steps(torch, fn, max(3, args.steps), 2, stream)
+        ref = _band_rows_oracle(kk.cpu().numpy(), xin, rows)
+        got = out[frames][:, rows].double().cpu().numpy()
+        e_orc = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        ops.tidas_forward_2d(kk, refl[:1].contiguous(), variant=capi.VARIANT_DIRECT, out=out[:1])
+        e_das = float((out[0].double() - das0).norm() / das0.norm())
+        front.append({"kz": kz, "taps": TAPS, "gemm_ms": m,
+                      "mpix_s": nf * nz * nx / (m * 1e-3) / 1e6,
+                      "speedup_vs_das_per_frame": das_ms_per_frame / (m / nf),
+                      "nrmse_vs_exact_das": e_das, "nrmse_vs_oracle": e_orc})
+        del kk, ws
+    return front
 
 
 def _band_rows_oracle(kern, x, rows):

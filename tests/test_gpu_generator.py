@@ -275,7 +275,7 @@ def test_learned_kernels_beat_shift_invariant_kernels_on_unseen_geometry():
     net = g.KernelMLP(batch=256)
     x16 = torch.empty((20000, 64), dtype=torch.bfloat16, device="cuda")
     net.encode(s, x16)
-    net.fit(x16, tgt, 100, _perms(100, 20000, 5), lr0=1e-3)
+    net.fit(x16, tgt, 200, _perms(200, 20000, 5), lr0=1e-3)
     fnum, ang = 1.7, 7.5 * math.pi / 180.0          # not a training draw
     sub = dict(geom, nz=64, z0=geom["z0"] + 400 * geom["dz"])  # 64 rows x 512 columns
     smp = g.grid_samples(sub, fnum, ang)
@@ -294,14 +294,20 @@ def test_learned_kernels_beat_shift_invariant_kernels_on_unseen_geometry():
     err_mixed = np.linalg.norm(host(mixed)[:, :63] - ex[:, :63], axis=1) / \
         np.linalg.norm(ex[:, :63], axis=1)
     assert err_mixed.max() <= 0.02 + 1e-6
-    # the network's own kernels, before any fallback: on average and on most
-    # pixels closer to the exact kernels than the shift-invariant ones, and
-    # good enough (NRMSE <= 2 %) to serve most of the grid without fallback
+    # the network's own kernels, before any fallback (200 epochs: mean NRMSE
+    # about 1.6 % against 12.8 % for the shift-invariant kernels, 25 % of the
+    # pixels above 2 %).  Near the centre column the shift-invariant kernel is
+    # the exact one, so the gain is claimed where one kernel per row breaks
+    # down: on pixels whose shift-invariant NRMSE exceeds 2 % (a third of the
+    # slab) the learned kernel must be the closer one almost everywhere.
     e_l = host(err_l)
     assert e_l.mean() < 0.5 * err_si.mean(), (e_l.mean(), err_si.mean())
-    assert float((e_l < err_si).mean()) > 0.5
+    broken = err_si > 0.02
+    assert broken.sum() > 1000
+    win = float((e_l[broken] < err_si[broken]).mean())
+    assert win > 0.95, win
     fallback = float((e_l > 0.02).mean())
-    assert fallback < 0.5, fallback
+    assert fallback < 0.4, fallback
 
 
 def test_checkpoint_resume_matches_an_uninterrupted_run(tmp_path):
