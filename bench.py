@@ -369,7 +369,8 @@ def run_ours(args):
 
     # ---- other DAS cases (not the headline)
     sub = {}
-    for nf, dt in ((1, torch.float16), (8, torch.float16), (1, torch.float32), (8, torch.float32)):
+    for nf, dt in ((1, torch.float16), (8, torch.float16), (1, torch.float32), (8, torch.float32),
+                   (64, torch.float32)):
         P = P16 if dt == torch.float16 else ops.DasPlan(g, rf_dtype=torch.float32)
         x = rf[:nf].float().contiguous() if dt == torch.float32 else rf[:nf].contiguous()
         y = torch.empty(P.img_shape(nf), device="cuda")

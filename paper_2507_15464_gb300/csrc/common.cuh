@@ -129,6 +129,7 @@ namespace tidas {
 int launch_delay_table(const Plan& P, int angle, int32_t* idx, float* frac, cudaStream_t st);
 int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
 int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
+int plan_staging(const Plan& P, size_t need, void** out);
 int das_tc_prepare(Plan& P);
 int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaStream_t st);
 int launch_synthesize(const Plan& P, const double* pos, const float* amp, int n_scat, int nf,

@@ -670,6 +670,22 @@ __global__ void das_tc_round_kernel(int A, int NE, int tiles, int* __restrict__ 
     }
 }
 
+// The plan's staging buffer of das_forward (the repacked batch of either DAS
+// path), grown to `need` bytes on demand.  cudaFree / cudaMalloc synchronise
+// the device, which is why das_forward calls on one plan must not overlap.
+int plan_staging(const Plan& P, size_t need, void** out) {
+    std::lock_guard<std::mutex> lock(P.tc_ws_mutex);
+    if (need > P.tc_ws_bytes) {
+        if (P.tc_ws) TIDAS_CUDA(cudaFree(P.tc_ws));
+        P.tc_ws = nullptr;
+        P.tc_ws_bytes = 0;
+        TIDAS_CUDA(cudaMalloc(&P.tc_ws, need));
+        P.tc_ws_bytes = need;
+    }
+    *out = P.tc_ws;
+    return TIDAS_OK;
+}
+
 // Build the window table of an FP16 plan (once, at plan creation).
 int das_tc_prepare(Plan& P) {
     const DasDev& d = P.dev;
@@ -722,17 +738,9 @@ int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_
     const int Sp = packed_len(d.n_samples);
     const int FT = (nf + NF - 1) / NF;
     const size_t need = (size_t)FT * R * Sp * NF * 2;
-    {
-        std::lock_guard<std::mutex> lock(P.tc_ws_mutex);
-        if (need > P.tc_ws_bytes) {
-            if (P.tc_ws) TIDAS_CUDA(cudaFree(P.tc_ws));
-            P.tc_ws = nullptr;
-            P.tc_ws_bytes = 0;
-            TIDAS_CUDA(cudaMalloc(&P.tc_ws, need));
-            P.tc_ws_bytes = need;
-        }
-    }
-    __half* packed = (__half*)P.tc_ws;
+    void* ws = nullptr;
+    if (int rc0 = plan_staging(P, need, &ws)) return rc0;
+    __half* packed = (__half*)ws;
     das_tc_pack_kernel<<<(unsigned)((size_t)FT * R * (Sp / kPackS)), 256, 0, st>>>(
         (const __half*)rf, packed, nf, R, d.n_samples, Sp, NF);
     int rc = check_launch("das_tc_pack_kernel");

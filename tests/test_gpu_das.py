@@ -204,6 +204,29 @@ def test_das_ragged_grid_and_out_of_record_taps(interp):
         assert rel_l2(img[f], O.das(rf[f])) <= TOL32
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("interp", [0, 1])
+def test_das_frames_innermost_batches(dtype, interp):
+    # batches of 2 .. 20 frames are restaged with the frames innermost and
+    # read as frame vectors (tiles of 4, 8 or 16 frames, the last one
+    # ragged); a ragged grid whose deepest taps leave the record exercises the
+    # bounds-checked variant.  Every frame must equal the single-frame path
+    # (rounding order differs: the apodization is folded into the tap
+    # weights) and the oracle.
+    g = presets.geometry("pw64_single", nx=100, nz=77, interp=interp, n_samples=1100)
+    tdt = torch.float32 if dtype == "f32" else torch.float16
+    P, O = plan(g, tdt), oracle(g)
+    for nf in (2, 5, 8, 9, 13, 20):
+        rf = generators.standard_normal((nf, 1, 64, 1100), (23, nf), np.float32)
+        x = to_dev(rf, tdt)
+        img = host(P.forward(x))
+        xs = host(x)  # the values the GPU sees (FP16-rounded for f16)
+        for f in sorted({0, nf // 2, nf - 1}):
+            one = host(P.forward(x[f:f + 1].contiguous()))[0]
+            assert rel_l2(img[f], one) <= 1e-6, (nf, f)
+            assert rel_l2(img[f], O.das(xs[f])) <= TOL32, (nf, f)
+
+
 def test_das_full_aperture_no_fnum():
     # whole array, unit weights: receive excess paths reach ~360 samples, where
     # the FP32 split delay is least accurate; band-limited channel data
