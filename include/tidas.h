@@ -136,7 +136,11 @@ int das_synthesize_adjoint(das_plan plan, const void* rf, float* refl, int32_t n
  * aperture w = cos^2(pi (x - x_n) F# / z) for |x - x_n| <= z / (2 F#)
  * (Section 3.1 fixes the f-number).  Accumulation is FP32.
  *   rf  [n_frames][n_angles][n_elem][n_samples], plan's rf_dtype
- *   img [n_frames][nz][nx] float32 (output) */
+ *   img [n_frames][nz][nx] float32 (output)
+ * FP16 plans restage batches of two or more frames in a staging buffer the
+ * plan owns (frames innermost; the tensor-core repack at >= 16 frames, see
+ * DAS_OPT_TENSOR_CORES), allocated on first use and grown for larger
+ * batches: das_forward calls on one FP16 plan must not overlap in time. */
 int das_forward(das_plan plan, const void* rf, float* img, int32_t n_frames, void* stream);
 
 /* Transpose of das_forward (B^T), for FP32 channel data plans:
