@@ -437,12 +437,19 @@ int tidas_mlp_infer(const double* samples, int64_t n, const float* lo4, const fl
  *   kernels  [nz][nx][kz][ld] float32, element (j, s, u, t) at
  *            ((j nx + s) kz + u) ld + t; 1 <= taps <= 64, ld >= taps,
  *            1 <= kz <= 64
- *   refl     [n_frames][nz][nx] float32 (variant TIDAS_VARIANT_DIRECT: FP32
- *            CUDA cores, the only variant of these calls)
+ *   refl     [n_frames][nz][nx]: float32 for TIDAS_VARIANT_DIRECT (FP32 CUDA
+ *            cores), bfloat16 for TIDAS_VARIANT_GEMM_BF16 (forward only:
+ *            tcgen05 GEMMs, per output row and 128-column tile, over the kz
+ *            slices and three 64-column input chunks, the B operand built
+ *            from the chunk's per-pixel kernels rounded to BF16; FP32 sums;
+ *            nx % 8 == 0, 16-byte aligned refl and img; its stream-ordered
+ *            scratch, the input repacked as for tidas_forward_2d, comes from
+ *            cudaMallocAsync on `stream` and is freed after the call's kernels)
  *   img      [n_frames][nz][nx] float32 (overwritten)
- * tidas_forward_varying is the row form (kz = 1, kernels [nz * nx][ld]).
- * tidas_adjoint_varying_2d is the transpose: each pixel correlates img with
- * its own kernel, refl[f][j][s] = sum_{u,t} K[j][s][u][t] img[f][j+u-kz/2][s+t-taps/2].
+ * tidas_forward_varying is the row form (kz = 1, kernels [nz * nx][ld],
+ * FP32 direct).  tidas_adjoint_varying_2d (FP32 direct) is the transpose:
+ * each pixel correlates img with its own kernel,
+ * refl[f][j][s] = sum_{u,t} K[j][s][u][t] img[f][j+u-kz/2][s+t-taps/2].
  * Other variants return TIDAS_ERR_UNSUPPORTED.  Sums run in a fixed order. */
 int tidas_forward_varying(const float* kernels, int32_t ld, int32_t taps, int32_t nz, int32_t nx,
                           const float* refl, float* img, int32_t n_frames, void* stream);

@@ -879,6 +879,353 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
     return rc;
 }
 
+// ------------------------------------ spatially varying band kernels (tcgen05)
+// Eq. (2.13) with a kernel per pixel (each input pixel adds its own
+// single-scatterer image):
+//   y[f][i][x] = sum_{u,t} K[j][s][u][t] r[f][j][s],  j = i - u + kz/2,  s = x - t + taps/2.
+// Work item = (output row i, 128-column tile, up to two 128-frame tiles).
+// The K loop runs over the band slices u and the tile's input chunks
+// q = 2 xt + c, c = 0..2, whose columns [64 q - 32, 64 q + 32) cover every s
+// the tile reads.  A step multiplies the packed input chunk of row j (the 2D
+// band GEMM's operand image, 128 frames x 64 columns per frame tile) by a B
+// tile that the builder warps write from the kernels of the chunk's pixels,
+//     B[x][s] = K[j][s][u][x - s + taps/2]   (zero outside the taps),
+// 128 output columns x 64 input columns, K-major, 128-byte swizzle: row x of
+// B collects, for each input pixel, the tap that reaches x.  The kernel
+// varies from pixel to pixel, so unlike the shift-invariant kernels no B
+// tile serves two steps; the builders' loads are coalesced (consecutive
+// lanes take consecutive output columns, i.e. consecutive taps of one
+// pixel's kernel).
+//   warp 0      bulk-copy producer of the input chunks (3-stage ring)
+//   warp 1      tensor-memory owner; lane 0 issues the MMAs
+//   warps 2-9   B tiles (double buffered)
+//   warps 10-13 epilogue: tensor memory -> swizzled staging tile -> TMA store
+// Accumulators (two frame tiles x 128 columns) are double buffered, so the
+// epilogue of one item overlaps the MMAs of the next.
+namespace vgem {
+constexpr int kStages = 3;
+constexpr int kMaxFT = 2;
+constexpr int kStageBytes = kMaxFT * gemm::kChunkBytes;  // 32 KB
+constexpr int kBBufs = 2;
+constexpr int kBuilders = 8;
+constexpr int kBuilder0 = 2;
+constexpr int kEpi0 = kBuilder0 + kBuilders;  // 10
+constexpr int kWarps = kEpi0 + 4;
+constexpr int kThreads = 32 * kWarps;
+constexpr uint32_t kAccCols = kMaxFT * gemm::kN;  // 256
+constexpr uint32_t kTmemCols = 2 * kAccCols;      // 512
+constexpr size_t kOffA = 0;
+constexpr size_t kOffB = kOffA + (size_t)kStages * kStageBytes;
+constexpr size_t kOffO = kOffB + (size_t)kBBufs * gemm::kBTileBytes;
+constexpr size_t kOffBar = kOffO + (size_t)4 * 2 * gemm::kOutTileBytes;
+constexpr size_t kSmem = 1024 + kOffBar + 256;
+static_assert(kSmem <= 227 * 1024, "shared memory");
+constexpr int kWaitEmpty = 111, kWaitFull = 112, kWaitB = 113, kWaitBFree = 114, kWaitAcc = 115,
+              kWaitAccFree = 116, kWaitDrain = 117, kWaitDone = 118;
+
+struct VItem {
+    int i, xt, ft0, nft, lo, hi, nc;
+};
+// items: row fastest, so that neighbouring CTAs share input rows in L2
+__device__ __forceinline__ VItem vdecode(int it, int nz, int ntiles, int nm, int kz, int nx) {
+    VItem v;
+    v.i = it % nz;
+    v.xt = (it / nz) % ntiles;
+    v.ft0 = (it / (nz * ntiles)) * kMaxFT;
+    v.nft = min(kMaxFT, nm - v.ft0);
+    u_range2d(v.i, kz, nz, false, v.lo, v.hi);
+    // input chunks of the tile that start inside the row
+    v.nc = 0;
+    for (int c = 0; c < 3; ++c)
+        if (64 * (2 * v.xt + c) - 32 < nx) v.nc = c + 1;
+    return v;
+}
+}  // namespace vgem
+
+__global__ void __launch_bounds__(vgem::kThreads, 1)
+    tidas_varying_gemm_kernel(const uint8_t* __restrict__ packed,
+                              const __grid_constant__ CUtensorMap tmap_out,
+                              const float* __restrict__ kern, int ld, int kz, int taps, int nz,
+                              int nx, int nf) {
+    using namespace gemm;
+    using namespace vgem;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base + vgem::kOffA;
+    uint8_t* sB = base + vgem::kOffB;
+    uint8_t* sO = base + vgem::kOffO;
+    uint64_t* full = (uint64_t*)(base + vgem::kOffBar);
+    uint64_t* empty = full + vgem::kStages;
+    uint64_t* b_full = empty + vgem::kStages;
+    uint64_t* b_empty = b_full + kBBufs;
+    uint64_t* acc_full = b_empty + kBBufs;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* done = acc_empty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* s_abort = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cz = kz / 2, cx = taps / 2;
+    const int ntiles = (nx + kN - 1) / kN;
+    const int nm = (nf + kM - 1) / kM;
+    const int nq = gemm2::n_chunks(nx);
+    const int total = nz * ntiles * ((nm + kMaxFT - 1) / kMaxFT);
+    const int it_begin = blockIdx.x, it_step = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < vgem::kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < kBBufs; ++s) {
+            mbar_init(&b_full[s], kBuilders);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+        }
+        mbar_init(done, 1);
+        *s_abort = 0;
+        fence_barrier_init();
+        prefetch_tensormap(&tmap_out);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, vgem::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ bulk-copy producer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            int issued = 0;
+            bool stop = false;
+            for (int it = it_begin; it < total && !stop; it += it_step) {
+                const VItem I = vdecode(it, nz, ntiles, nm, kz, nx);
+                for (int u = I.lo; u <= I.hi && !stop; ++u) {
+                    const int j = I.i - u + cz;
+                    for (int c = 0; c < I.nc; ++c) {
+                        if (!mbar_wait_or_abort(&empty[st], ph ^ 1, s_abort, &g_wait_error,
+                                                vgem::kWaitEmpty)) {
+                            stop = true;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[st], (uint32_t)(I.nft * kChunkBytes));
+                        const int q = 2 * I.xt + c;
+                        for (int f = 0; f < I.nft; ++f)
+                            bulk_load(sA + st * vgem::kStageBytes + f * kChunkBytes,
+                                      packed + (((size_t)j * nm + I.ft0 + f) * nq + q) * kChunkBytes,
+                                      kChunkBytes, &full[st]);
+                        if (++st == (uint32_t)vgem::kStages) { st = 0; ph ^= 1; }
+                        ++issued;
+                    }
+                }
+            }
+            if (*s_abort) {
+                // let issued copies land before shared memory is released
+                for (int k = 0; k < min(issued, vgem::kStages); ++k) {
+                    st = (st == 0) ? vgem::kStages - 1 : st - 1;
+                    if (st == (uint32_t)vgem::kStages - 1) ph ^= 1;
+                    mbar_wait(&full[st], ph, &g_wait_error, vgem::kWaitDrain);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t st = 0, ph = 0;
+            int step = 0, k = 0;
+            bool stop = false;
+            for (int it = it_begin; it < total && !stop; it += it_step, ++k) {
+                const VItem I = vdecode(it, nz, ntiles, nm, kz, nx);
+                const int ab = k & 1;
+                if (!mbar_wait_or_abort(&acc_empty[ab], ((k >> 1) & 1) ^ 1, s_abort, &g_wait_error,
+                                        vgem::kWaitAccFree))
+                    break;
+                tc_fence_after();
+                bool first = true;
+                for (int u = I.lo; u <= I.hi && !stop; ++u) {
+                    for (int c = 0; c < I.nc; ++c, ++step) {
+                        const int b = step & 1;
+                        if (!mbar_wait_or_abort(&full[st], ph, s_abort, &g_wait_error,
+                                                vgem::kWaitFull) ||
+                            !mbar_wait_or_abort(&b_full[b], (step >> 1) & 1, s_abort,
+                                                &g_wait_error, vgem::kWaitB)) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t db = desc_sw128_kmajor(smem_u32(sB + b * kBTileBytes));
+                        for (int f = 0; f < I.nft; ++f) {
+                            const uint64_t da = desc_sw128_kmajor(
+                                smem_u32(sA + st * vgem::kStageBytes + f * kChunkBytes));
+                            const uint32_t d = tmem_base + (uint32_t)(ab * vgem::kAccCols) +
+                                               (uint32_t)(f * kN);
+#pragma unroll
+                            for (int kk = 0; kk < kKC / 16; ++kk)
+                                mma_f16(d, da + 2 * kk, db + 2 * kk, kIdesc,
+                                        (first && kk == 0) ? 0u : 1u);
+                        }
+                        first = false;
+                        mma_commit(&empty[st]);
+                        mma_commit(&b_empty[b]);
+                        if (++st == (uint32_t)vgem::kStages) { st = 0; ph ^= 1; }
+                    }
+                }
+                if (stop) break;
+                mma_commit(&acc_full[ab]);
+            }
+            // every MMA this thread issued has completed before tensor memory
+            // is released (also after an abort)
+            mma_commit(done);
+            mbar_wait(done, 0, &g_wait_error, vgem::kWaitDone);
+        }
+        __syncwarp();
+    } else if (warp < kEpi0) {
+        // --------------------------------------------------------- B tiles
+        // thread: output row x = 32 (wb % 4) + lane of the tile, 16-byte
+        // chunks 4 (wb / 4) .. + 3 (input columns 8 k16 .. + 7 of the chunk)
+        const int wb = warp - kBuilder0;
+        const int x_rel = 32 * (wb & 3) + lane;
+        const int k16_0 = 4 * (wb >> 2);
+        int step = 0;
+        bool stop = false;
+        for (int it = it_begin; it < total && !stop; it += it_step) {
+            const VItem I = vdecode(it, nz, ntiles, nm, kz, nx);
+            const int x = kN * I.xt + x_rel;
+            for (int u = I.lo; u <= I.hi && !stop; ++u) {
+                const int j = I.i - u + cz;
+                const float* krow = kern + (size_t)j * nx * kz * ld + (size_t)u * ld;
+                for (int c = 0; c < I.nc; ++c, ++step) {
+                    const int b = step & 1;
+                    const int s0 = 64 * (2 * I.xt + c) - 32;
+                    // this thread's 32 taps, loaded before the buffer is free
+                    float v[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int sx = s0 + 8 * k16_0 + e;
+                        const int t = x - sx + cx;
+                        v[e] = (t >= 0 && t < taps && sx >= 0 && sx < nx)
+                                   ? __ldg(krow + (size_t)sx * kz * ld + t)
+                                   : 0.f;
+                    }
+                    bool ok = mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
+                                                 &g_wait_error, vgem::kWaitBFree);
+                    if (ok) {
+                        uint8_t* dst = sB + b * kBTileBytes;
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            uint32_t w4[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const __nv_bfloat162 p2 =
+                                    __floats2bfloat162_rn(v[8 * h + 2 * e], v[8 * h + 2 * e + 1]);
+                                w4[e] = *reinterpret_cast<const uint32_t*>(&p2);
+                            }
+                            *reinterpret_cast<uint4*>(dst + sw128_offset(x_rel, 8 * (k16_0 + h))) =
+                                make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                        }
+                        fence_proxy_async_smem();
+                    }
+                    __syncwarp();
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        stop = true;
+                        break;
+                    }
+                    if (lane == 0) mbar_arrive(&b_full[b]);
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------- epilogue
+        const int quarter = warp & 3;  // tensor-memory lanes 32 quarter .. + 31
+        uint8_t* stage_buf = sO + (size_t)(warp - kEpi0) * 2 * kOutTileBytes;
+        int k = 0, q = 0;
+        for (int it = it_begin; it < total; it += it_step, ++k) {
+            const VItem I = vdecode(it, nz, ntiles, nm, kz, nx);
+            const int ab = k & 1;
+            if (!mbar_wait_or_abort(&acc_full[ab], (k >> 1) & 1, s_abort, &g_wait_error,
+                                    vgem::kWaitAcc))
+                break;
+            tc_fence_after();
+            for (int f = 0; f < I.nft; ++f) {
+#pragma unroll 1
+                for (int jc = 0; jc < kN / 32; ++jc, ++q) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                           (uint32_t)(ab * vgem::kAccCols + f * kN + jc * 32),
+                                       r);
+                    tmem_ld_wait();
+                    uint8_t* tile = stage_buf + (q & 1) * kOutTileBytes;
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; ++c4)
+                        *reinterpret_cast<uint4*>(tile + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                            make_uint4(r[4 * c4], r[4 * c4 + 1], r[4 * c4 + 2], r[4 * c4 + 3]);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_3d(&tmap_out, tile, kN * I.xt + jc * 32, I.i,
+                                     (I.ft0 + f) * kM + quarter * 32);
+                        bulk_commit();
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+        if (lane == 0) bulk_wait<0>();
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, vgem::kTmemCols);
+    }
+}
+
+int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int nz, int nx,
+                              const void* in, float* out, int nf, cudaStream_t st) {
+    CUtensorMap map_out;
+    int rc = make_map_3d(&map_out, out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nz, nx, nf, 32, 32,
+                         CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    const int nm = (nf + gemm::kM - 1) / gemm::kM, nq = gemm2::n_chunks(nx);
+    const size_t images = (size_t)nz * nm * nq;
+    if (images > (size_t)INT_MAX)
+        return set_error(TIDAS_ERR_UNSUPPORTED, "tidas varying GEMM: %zu chunk images", images);
+    uint8_t* packed = nullptr;
+    TIDAS_CUDA(cudaMallocAsync((void**)&packed, band_pack_bytes(nz, nx, nf), st));
+    tidas_band_pack_kernel<<<(unsigned)images, 256, 0, st>>>((const __nv_bfloat16*)in, packed, nz,
+                                                             nx, nf, nm, nq);
+    rc = check_launch("tidas_band_pack_kernel");
+    if (rc == TIDAS_OK) {
+        const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
+        const int items = nz * ntiles * ((nm + vgem::kMaxFT - 1) / vgem::kMaxFT);
+        const int grid = items < sm_count() ? items : sm_count();
+        rc = check_cuda(cudaFuncSetAttribute(tidas_varying_gemm_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)vgem::kSmem),
+                        "cudaFuncSetAttribute(tidas_varying_gemm_kernel)");
+        if (rc == TIDAS_OK) {
+            tidas_varying_gemm_kernel<<<grid, vgem::kThreads, vgem::kSmem, st>>>(
+                packed, map_out, kern, ld, kz, taps, nz, nx, nf);
+            rc = check_launch("tidas_varying_gemm_kernel");
+        }
+    }
+    cudaFreeAsync(packed, st);
+    return rc;
+}
+
 }  // namespace tidas
 
 namespace tidas {

@@ -9,8 +9,10 @@
 //   adjoint  r[f][j][s] = sum_{u,t} K[j][s][u][t] y[f][j + u - kz/2][s + t - taps/2]
 // Kernels are the INPUT pixel's (the scatterer's), stored [nz][nx][kz][ld].
 //
-// FP32 CUDA-core form.  One block per (128-column tile, row, frame chunk);
-// per band slice u the block stages the kernels its tile needs (odd row
+// The tcgen05 form of the forward map (BF16 operands, FP32 sums) is in
+// tidas_gemm.cu; this file holds the FP32 CUDA-core form and the entry
+// points.  One block per (128-column tile, row, frame chunk); per band
+// slice u the block stages the kernels its tile needs (odd row
 // stride, so a warp's lanes, which read kernels of consecutive pixels, hit
 // distinct banks) and the matching input line of 8 frames, then each thread
 // accumulates one output column for 8 frames in registers.
@@ -127,19 +129,30 @@ int launch_varying_direct(bool adj, const float* kern, int ld, int kz, int taps,
 }
 
 int varying_args(const char* who, const float* kern, int ld, int kz, int taps, int nz, int nx,
-                 const void* in, const void* out, int nf, int variant) {
+                 const void* in, const void* out, int nf, int variant, bool gemm_ok) {
     TIDAS_REQUIRE(kern && in && out, "%s: null pointer", who);
     TIDAS_REQUIRE(taps >= 1 && taps <= kVMaxTaps && kz >= 1 && kz <= kVMaxKz && ld >= taps,
                   "%s: need 1 <= taps <= %d, 1 <= kz <= %d, ld >= taps (taps=%d kz=%d ld=%d)", who,
                   kVMaxTaps, kVMaxKz, taps, kz, ld);
     TIDAS_REQUIRE(nz >= 1 && nx >= 1 && nf >= 1 && nz <= 65535,
                   "%s: need nz, nx, n_frames >= 1 and nz <= 65535", who);
+    if (variant == TIDAS_VARIANT_GEMM_BF16 && gemm_ok) {
+        if (nx % 8 != 0)
+            return set_error(TIDAS_ERR_UNSUPPORTED, "%s: the GEMM variant needs nx %% 8 == 0", who);
+        TIDAS_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0,
+                      "%s: the GEMM variant needs 16-byte aligned arrays", who);
+        return 0;
+    }
     if (variant != TIDAS_VARIANT_DIRECT)
         return set_error(TIDAS_ERR_UNSUPPORTED, "%s: variant %d not available", who, variant);
     return 0;
 }
 
 }  // namespace
+
+// tcgen05 form of the forward map (tidas_gemm.cu)
+int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int nz, int nx,
+                              const void* in, float* out, int nf, cudaStream_t st);
 }  // namespace tidas
 
 using namespace tidas;
@@ -148,7 +161,7 @@ extern "C" int tidas_forward_varying(const float* kernels, int32_t ld, int32_t t
                                      int32_t nx, const float* refl, float* img, int32_t n_frames,
                                      void* stream) {
     if (int rc = varying_args("tidas_forward_varying", kernels, ld, 1, taps, nz, nx, refl, img,
-                              n_frames, TIDAS_VARIANT_DIRECT))
+                              n_frames, TIDAS_VARIANT_DIRECT, false))
         return rc;
     return launch_varying_direct(false, kernels, ld, 1, taps, nz, nx, refl, img, n_frames,
                                  (cudaStream_t)stream);
@@ -158,8 +171,11 @@ extern "C" int tidas_forward_varying_2d(const float* kernels, int32_t ld, int32_
                                         int32_t nz, int32_t nx, const void* refl, float* img,
                                         int32_t n_frames, int32_t variant, void* stream) {
     if (int rc = varying_args("tidas_forward_varying_2d", kernels, ld, kz, taps, nz, nx, refl,
-                              img, n_frames, variant))
+                              img, n_frames, variant, true))
         return rc;
+    if (variant == TIDAS_VARIANT_GEMM_BF16)
+        return launch_tidas_varying_gemm(kernels, ld, kz, taps, nz, nx, refl, img, n_frames,
+                                         (cudaStream_t)stream);
     return launch_varying_direct(false, kernels, ld, kz, taps, nz, nx, (const float*)refl, img,
                                  n_frames, (cudaStream_t)stream);
 }
@@ -168,7 +184,7 @@ extern "C" int tidas_adjoint_varying_2d(const float* kernels, int32_t ld, int32_
                                         int32_t nz, int32_t nx, const void* img, float* refl,
                                         int32_t n_frames, int32_t variant, void* stream) {
     if (int rc = varying_args("tidas_adjoint_varying_2d", kernels, ld, kz, taps, nz, nx, img,
-                              refl, n_frames, variant))
+                              refl, n_frames, variant, false))
         return rc;
     return launch_varying_direct(true, kernels, ld, kz, taps, nz, nx, (const float*)img, refl,
                                  n_frames, (cudaStream_t)stream);

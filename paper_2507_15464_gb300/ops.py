@@ -264,7 +264,8 @@ def _varying(fn, kernels, x, variant, out=None):
         nz, nx, kz, taps = kernels.shape
     nf = x.shape[0]
     _need(kernels, torch.float32, tuple(kernels.shape), "kernels")
-    _need(x, torch.float32, (nf, nz, nx), "input")
+    want = torch.bfloat16 if variant == capi.VARIANT_GEMM_BF16 else torch.float32
+    _need(x, want, (nf, nz, nx), "input")
     out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
                                                   device=x.device)
     fn(_ptr(kernels), taps, kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
@@ -274,7 +275,9 @@ def _varying(fn, kernels, x, variant, out=None):
 def tidas_forward_varying(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
     """Eq. (2.13) with a kernel per pixel (each pixel adds its own
     single-scatterer image): kernels [nz, nx, taps] (row form) or
-    [nz, nx, kz, taps] (band form), refl [B, nz, nx] -> img [B, nz, nx]."""
+    [nz, nx, kz, taps] (band form), refl [B, nz, nx] -> img [B, nz, nx].
+    VARIANT_DIRECT: FP32 refl on CUDA cores; VARIANT_GEMM_BF16: BF16 refl on
+    the tcgen05 tensor cores."""
     return _varying(capi.tidas_forward_varying_2d, kernels, refl, variant, out)
 
 

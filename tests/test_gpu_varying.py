@@ -5,7 +5,9 @@ against the FP64 oracle, through the C ABI.
 FP32 CUDA-core path: relative L2 <= 1e-5 against the oracle on identical
 inputs (FP32 FMA chains of at most kz x taps terms); a unit reflector
 returns its own kernel bit for bit (one product by 1.0, the other terms
-exact zeros).
+exact zeros).  tcgen05 GEMM path: <= 5e-3 against the oracle on the same
+BF16 input values (the kernels are rounded to BF16, unit roundoff 2^-8;
+FP32 sums).
 """
 import numpy as np
 import pytest
@@ -113,3 +115,44 @@ def test_varying_rejects_unsupported_requests():
     with pytest.raises(capi.TidasError) as e:
         o.tidas_forward_varying(to_dev(big), to_dev(r))
     assert e.value.code == capi.TIDAS_ERR_ARG
+
+
+# (frames, rows, columns, kz, taps) of the GEMM path: one and three frame
+# tiles (two per item, then a ragged one), partial column tiles, taps 1 / odd
+# / 64, kz 1 .. 16
+GEMM_CASES = [(3, 6, 256, 1, 63), (130, 5, 200, 4, 31), (257, 4, 64, 3, 64), (2, 20, 512, 8, 63),
+              (1, 9, 136, 16, 7), (5, 3, 8, 2, 1)]
+
+
+@pytest.mark.parametrize("nf,nz,nx,kz,taps", GEMM_CASES)
+def test_varying_gemm_matches_oracle(nf, nz, nx, kz, taps):
+    import oracle
+    from paper_2507_15464_gb300 import capi
+    o = ops()
+    k, r = _case(nf, nz, nx, kz, taps, 76 + nx + kz)
+    x16 = to_dev(r).to(torch.bfloat16)
+    y = host(o.tidas_forward_varying(to_dev(k), x16, variant=capi.VARIANT_GEMM_BF16))
+    frames = sorted({0, nf // 2, nf - 1})
+    ref = oracle.tidas_conv_varying(k, host(x16)[frames])
+    assert rel_l2(y[frames], ref) <= 5e-3
+    # and close to the FP32 direct path on every frame
+    yd = host(o.tidas_forward_varying(to_dev(k), x16.float()))
+    assert rel_l2(y, yd) <= 5e-3
+
+
+def test_varying_gemm_full_width_band_slab():
+    # the workload's 512-column rows with 8 x 63 band kernels and 256 frames
+    # (two frame tiles per item); the oracle runs on a slab of rows for the
+    # first and last frames, and the rows whose band lies in the slab compare
+    import oracle
+    from paper_2507_15464_gb300 import capi
+    o = ops()
+    nf, nz, nx, kz, taps = 256, 64, 512, 8, 63
+    k, r = _case(nf, nz, nx, kz, taps, 77)
+    x16 = to_dev(r).to(torch.bfloat16)
+    y = host(o.tidas_forward_varying(to_dev(k), x16, variant=capi.VARIANT_GEMM_BF16))
+    lo, hi = 20, 50
+    xs = host(x16)[[0, nf - 1]][:, lo:hi]
+    ref = oracle.tidas_conv_varying(k[lo:hi], xs)
+    inner = slice(kz, hi - lo - kz)
+    assert rel_l2(y[[0, nf - 1]][:, lo:hi][:, inner], ref[:, inner]) <= 5e-3
