@@ -365,6 +365,17 @@ int tidas_axpby(const float* a, const float* b, float* out, int64_t n, float alp
 int tidas_psf_batch(das_plan plan, const double* samples, int32_t n, int32_t taps, float* out,
                     int32_t ldo, float* norm, void* stream);
 
+/* Band patches of the same exact PSFs (Eq. (2.6)-(2.7) with the axial extent
+ * kept): for sample i the image of its unit scatterer at rows
+ * z + (u - kz/2) dz and columns x + (t - taps/2) dx, u < kz, t < taps, of the
+ * plan's grid spacing, written to out[i][u * ldk + t] (zero for
+ * taps <= t < ldk and columns >= kz * ldk); the row u = kz/2 equals
+ * tidas_psf_batch's row.  norm as for tidas_psf_batch.  1 <= kz <= 64,
+ * ldk >= taps, kz * ldk <= ldo <= 65536. */
+int tidas_psf_batch_2d(das_plan plan, const double* samples, int32_t n, int32_t kz, int32_t taps,
+                       int32_t ldk, float* out, int32_t ldo, float* norm, void* stream);
+
+
 /* out[i] = sum of the receive apodization weights at (x, z) for F#
  * (samples as tidas_psf_batch; the kernel scale).  Evaluated in FP32. */
 int tidas_apod_sum(das_plan plan, const double* samples, int64_t n, float* out, void* stream);
@@ -442,7 +453,9 @@ int tidas_mlp_infer(const double* samples, int64_t n, const float* lo4, const fl
  *            tcgen05 GEMMs, per output row and 128-column tile, over the kz
  *            slices and three 64-column input chunks, the B operand built
  *            from the chunk's per-pixel kernels rounded to BF16; FP32 sums;
- *            nx % 8 == 0, 16-byte aligned refl and img; its stream-ordered
+ *            nx % 8 == 0, 16-byte aligned kernels, refl and img; kernels
+ *            whose pitch ld is not a multiple of 4 are first copied to a
+ *            padded stream-ordered scratch (ld % 4 == 0 avoids it); its stream-ordered
  *            scratch, the input repacked as for tidas_forward_2d, comes from
  *            cudaMallocAsync on `stream` and is freed after the call's kernels)
  *   img      [n_frames][nz][nx] float32 (overwritten)

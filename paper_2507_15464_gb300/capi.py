@@ -72,6 +72,7 @@ _SIG = {
                            ctypes.c_float, _P],
     "tidas_axpby": [_P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P],
     "tidas_psf_batch": [_P, _P, _I, _I, _P, _I, _P, _P],
+    "tidas_psf_batch_2d": [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P],
     "tidas_apod_sum": [_P, _P, ctypes.c_int64, _P, _P],
     "tidas_gemm_bf16": [_P, _P, _I, _I, _I, _P, _I, _P, _P, _I, _P],
     "tidas_transpose_bf16": [_P, _I, _I, _P, _P],

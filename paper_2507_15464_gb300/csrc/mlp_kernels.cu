@@ -341,7 +341,7 @@ __global__ void encode_kernel(const double* __restrict__ samples, int n, const f
 namespace tidas {
 struct PsfArgs {
     int n_elem, interp, n_samples, taps;
-    double pitch, c, fs, t0, dx;
+    double pitch, c, fs, t0, dx, dz;
     double thalf, beta, wcar;  // samples
 };
 
@@ -413,6 +413,61 @@ __global__ void psf_batch_kernel(PsfArgs A, const double* __restrict__ samples, 
         out[(size_t)i * ldo + t] = 0.f;
     }
     if (norm && t == 0) norm[i] = (float)s;
+}
+
+// Band patches of the same PSFs: the image of the unit scatterer of sample i
+// at rows z + (u - kz/2) dz and columns x + (t - taps/2) dx, written to
+// out[i][u * ldk + t] (zeros in the padding t >= taps); row u = kz/2 is the
+// row of psf_batch_kernel, evaluated by the same operations.  One block per
+// sample, threads over the (u, t) pairs.
+__global__ void psf_batch2d_kernel(PsfArgs A, const double* __restrict__ samples, int n, int kz,
+                                   int ldk, float* __restrict__ out, int ldo,
+                                   float* __restrict__ norm) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const double xs = samples[4 * i], z = samples[4 * i + 1], fnum = samples[4 * i + 2];
+    const double th = samples[4 * i + 3];
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    double s = 0.0;
+    for (int e = 0; e < A.n_elem; ++e) s += psf_apod(A, e, xs, z, fnum);
+    for (int q = threadIdx.x; q < ldo; q += blockDim.x) {
+        const int u = q / ldk, t = q - u * ldk;
+        if (u >= kz || t >= A.taps) {
+            out[(size_t)i * ldo + q] = 0.f;
+            continue;
+        }
+        const double xp = xs + (double)(t - A.taps / 2) * A.dx;
+        const double zp = z + (double)(u - kz / 2) * A.dz;
+        double acc = 0.0;
+        for (int e = 0; e < A.n_elem; ++e) {
+            const double w = psf_apod(A, e, xp, zp, fnum);
+            if (w == 0.0) continue;
+            const double up = psf_delay(A, sn, cs, e, xp, zp);
+            const double us = psf_delay(A, sn, cs, e, xs, z);
+            const double fl = floor(up);
+            const double phi = up - fl;
+            const int ii = (int)fl;
+            double v = 0.0;
+            if (A.interp == TIDAS_INTERP_CUBIC) {
+                float w0, w1, w2, w3;
+                keys_weights((float)phi, w0, w1, w2, w3);
+                const float wt[4] = {w0, w1, w2, w3};
+                for (int k = 0; k < 4; ++k) {
+                    const int m = ii - 1 + k;
+                    if (m < 0 || m >= A.n_samples) continue;
+                    v += (double)wt[k] * psf_pulse(A, (double)m - us);
+                }
+            } else {
+                if (ii >= 0 && ii < A.n_samples) v += (1.0 - phi) * psf_pulse(A, (double)ii - us);
+                if (ii + 1 >= 0 && ii + 1 < A.n_samples)
+                    v += phi * psf_pulse(A, (double)(ii + 1) - us);
+            }
+            acc += w * v;
+        }
+        out[(size_t)i * ldo + q] = (float)(norm ? acc / s : acc);
+    }
+    if (norm && threadIdx.x == 0) norm[i] = (float)s;
 }
 
 // per-pixel NRMSE of learned vs exact kernels; where it exceeds `thresh` the
@@ -489,6 +544,7 @@ static PsfArgs psf_args(const Plan& P, int taps) {
     A.fs = P.p.fs;
     A.t0 = P.p.t0;
     A.dx = P.p.dx;
+    A.dz = P.p.dz;
     A.thalf = P.thalf_samples;
     A.beta = P.beta_samples;
     A.wcar = P.wcar;
@@ -514,6 +570,19 @@ extern "C" int tidas_psf_batch(das_plan plan, const double* samples, int32_t n, 
     psf_batch_kernel<<<n, ((ldo + 31) / 32) * 32, 0, ST(stream)>>>(psf_args(P, taps), samples, n,
                                                                     out, ldo, norm);
     return check_launch("psf_batch_kernel");
+}
+
+extern "C" int tidas_psf_batch_2d(das_plan plan, const double* samples, int32_t n, int32_t kz,
+                                  int32_t taps, int32_t ldk, float* out, int32_t ldo, float* norm,
+                                  void* stream) {
+    TIDAS_REQUIRE(plan && samples && out, "tidas_psf_batch_2d: null pointer");
+    TIDAS_REQUIRE(n >= 1 && kz >= 1 && kz <= 64 && taps >= 1 && taps <= 255 && ldk >= taps &&
+                      ldo >= kz * ldk && ldo <= 65536,
+                  "tidas_psf_batch_2d: bad sizes");
+    const Plan& P = *(const Plan*)plan;
+    psf_batch2d_kernel<<<n, 256, 0, ST(stream)>>>(psf_args(P, taps), samples, n, kz, ldk, out, ldo,
+                                                  norm);
+    return check_launch("psf_batch2d_kernel");
 }
 
 extern "C" int tidas_apod_sum(das_plan plan, const double* samples, int64_t n, float* out,

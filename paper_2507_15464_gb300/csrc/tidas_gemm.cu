@@ -893,10 +893,13 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
 // 128 output columns x 64 input columns, K-major, 128-byte swizzle: row x of
 // B collects, for each input pixel, the tap that reaches x.  The kernel
 // varies from pixel to pixel, so unlike the shift-invariant kernels no B
-// tile serves two steps; the builders' loads are coalesced (consecutive
-// lanes take consecutive output columns, i.e. consecutive taps of one
-// pixel's kernel).
-//   warp 0      bulk-copy producer of the input chunks (3-stage ring)
+// tile serves two steps.  The chunk's kernel slice (64 pixels x slice u,
+// FP32) arrives in the step's stage by one TMA box beside the input chunks,
+// so that the builders read shared memory (consecutive lanes take
+// consecutive output columns, i.e. consecutive taps of one pixel: distinct
+// banks) and never wait on DRAM.
+//   warp 0      producer: input chunks (bulk copies) and kernel slices (TMA)
+//               into a 3-stage ring
 //   warp 1      tensor-memory owner; lane 0 issues the MMAs
 //   warps 2-9   B tiles (double buffered)
 //   warps 10-13 epilogue: tensor memory -> swizzled staging tile -> TMA store
@@ -905,7 +908,9 @@ int launch_tidas_gemm2d(const float* kern, int kz, int taps, bool adjoint, int n
 namespace vgem {
 constexpr int kStages = 3;
 constexpr int kMaxFT = 2;
-constexpr int kStageBytes = kMaxFT * gemm::kChunkBytes;  // 32 KB
+constexpr int kKOff = kMaxFT * gemm::kChunkBytes;         // kernel slice within a stage
+constexpr int kKBytes = 64 * 64 * 4;                      // 64 pixels x <= 64 FP32 taps
+constexpr int kStageBytes = kKOff + kKBytes;              // 48 KB
 constexpr int kBBufs = 2;
 constexpr int kBuilders = 8;
 constexpr int kBuilder0 = 2;
@@ -945,8 +950,8 @@ __device__ __forceinline__ VItem vdecode(int it, int nz, int ntiles, int nm, int
 __global__ void __launch_bounds__(vgem::kThreads, 1)
     tidas_varying_gemm_kernel(const uint8_t* __restrict__ packed,
                               const __grid_constant__ CUtensorMap tmap_out,
-                              const float* __restrict__ kern, int ld, int kz, int taps, int nz,
-                              int nx, int nf) {
+                              const __grid_constant__ CUtensorMap tmap_k, int boxw, int kz,
+                              int taps, int nz, int nx, int nf) {
     using namespace gemm;
     using namespace vgem;
     extern __shared__ uint8_t smem_raw[];
@@ -989,6 +994,7 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
         *s_abort = 0;
         fence_barrier_init();
         prefetch_tensormap(&tmap_out);
+        prefetch_tensormap(&tmap_k);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, vgem::kTmemCols);
@@ -1015,12 +1021,18 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
                             stop = true;
                             break;
                         }
-                        mbar_arrive_expect_tx(&full[st], (uint32_t)(I.nft * kChunkBytes));
+                        mbar_arrive_expect_tx(&full[st],
+                                              (uint32_t)(I.nft * kChunkBytes + boxw * 64 * 4));
                         const int q = 2 * I.xt + c;
                         for (int f = 0; f < I.nft; ++f)
                             bulk_load(sA + st * vgem::kStageBytes + f * kChunkBytes,
                                       packed + (((size_t)j * nm + I.ft0 + f) * nq + q) * kChunkBytes,
                                       kChunkBytes, &full[st]);
+                        // slice u of the chunk's 64 pixels j nx + 64 q - 32 ..; pixels
+                        // past either end of the grid are zero-filled, those of a
+                        // neighbouring row are masked by the builders
+                        tma_load_3d(sA + st * vgem::kStageBytes + vgem::kKOff, &tmap_k, &full[st],
+                                    0, u, j * nx + 64 * q - 32);
                         if (++st == (uint32_t)vgem::kStages) { st = 0; ph ^= 1; }
                         ++issued;
                     }
@@ -1095,29 +1107,33 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
         const int x_rel = 32 * (wb & 3) + lane;
         const int k16_0 = 4 * (wb >> 2);
         int step = 0;
+        uint32_t st = 0, ph = 0;
         bool stop = false;
         for (int it = it_begin; it < total && !stop; it += it_step) {
             const VItem I = vdecode(it, nz, ntiles, nm, kz, nx);
             const int x = kN * I.xt + x_rel;
             for (int u = I.lo; u <= I.hi && !stop; ++u) {
-                const int j = I.i - u + cz;
-                const float* krow = kern + (size_t)j * nx * kz * ld + (size_t)u * ld;
                 for (int c = 0; c < I.nc; ++c, ++step) {
                     const int b = step & 1;
                     const int s0 = 64 * (2 * I.xt + c) - 32;
-                    // this thread's 32 taps, loaded before the buffer is free
-                    float v[32];
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int sx = s0 + 8 * k16_0 + e;
-                        const int t = x - sx + cx;
-                        v[e] = (t >= 0 && t < taps && sx >= 0 && sx < nx)
-                                   ? __ldg(krow + (size_t)sx * kz * ld + t)
-                                   : 0.f;
-                    }
-                    bool ok = mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
+                    // the step's kernel slice has landed in its stage, and the
+                    // B buffer of two steps ago has been read by its MMAs
+                    bool ok = mbar_wait_or_abort(&full[st], ph, s_abort, &g_wait_error,
+                                                 vgem::kWaitFull) &&
+                              mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
                                                  &g_wait_error, vgem::kWaitBFree);
                     if (ok) {
+                        const float* ks =
+                            reinterpret_cast<const float*>(sA + st * vgem::kStageBytes + vgem::kKOff);
+                        float v[32];
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int sl = 8 * k16_0 + e;  // pixel s0 + sl of the slice
+                            const int sx = s0 + sl;
+                            const int t = x - sx + cx;
+                            v[e] = (t >= 0 && t < taps && sx >= 0 && sx < nx) ? ks[sl * boxw + t]
+                                                                              : 0.f;
+                        }
                         uint8_t* dst = sB + b * kBTileBytes;
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
@@ -1139,6 +1155,7 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
                         break;
                     }
                     if (lane == 0) mbar_arrive(&b_full[b]);
+                    if (++st == (uint32_t)vgem::kStages) { st = 0; ph ^= 1; }
                 }
             }
         }
@@ -1193,9 +1210,21 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
     }
 }
 
+// rows [rows][ld] -> [rows][ldp] (the first taps columns, zero padding)
+__global__ void pad_rows_kernel(const float* __restrict__ in, int ld, int taps, long long rows,
+                                float* __restrict__ out, int ldp) {
+    const long long n = rows * ldp;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long r = q / ldp;
+        const int t = (int)(q - r * ldp);
+        out[q] = t < taps ? in[r * ld + t] : 0.f;
+    }
+}
+
 int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int nz, int nx,
                               const void* in, float* out, int nf, cudaStream_t st) {
-    CUtensorMap map_out;
+    CUtensorMap map_out, map_k;
     int rc = make_map_3d(&map_out, out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nz, nx, nf, 32, 32,
                          CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
@@ -1203,11 +1232,51 @@ int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int n
     const size_t images = (size_t)nz * nm * nq;
     if (images > (size_t)INT_MAX)
         return set_error(TIDAS_ERR_UNSUPPORTED, "tidas varying GEMM: %zu chunk images", images);
+    // kernel rows of a pitch that TMA cannot address (not a multiple of 16
+    // bytes) are first copied to a padded scratch
+    const long long krows = (long long)nz * nx * kz;
+    float* kpad = nullptr;
+    int kld = ld;
+    if (ld % 4) {
+        kld = (taps + 3) & ~3;
+        TIDAS_CUDA(cudaMallocAsync((void**)&kpad, sizeof(float) * (size_t)krows * kld, st));
+        pad_rows_kernel<<<152 * 8, 256, 0, st>>>(kern, ld, taps, krows, kpad, kld);
+        rc = check_launch("pad_rows_kernel");
+        kern = kpad;
+    }
+    const int boxw = kld < 64 ? kld : 64;
+    if (rc == TIDAS_OK) {
+        // the kernels as [pixel][slice][kld] FP32: box = boxw taps x 1 slice x 64 pixels
+        EncodeTiledFn enc = encode_fn();
+        if (!enc) {
+            rc = set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        } else {
+            cuuint64_t dims[3] = {(cuuint64_t)kld, (cuuint64_t)kz, (cuuint64_t)nz * nx};
+            cuuint64_t strides[2] = {(cuuint64_t)kld * 4, (cuuint64_t)kz * kld * 4};
+            cuuint32_t box[3] = {(cuuint32_t)boxw, 1u, 64u};
+            cuuint32_t estr[3] = {1u, 1u, 1u};
+            CUresult r = enc(&map_k, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(kern),
+                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                rc = set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled (kernels) failed (%d)",
+                               (int)r);
+        }
+    }
     uint8_t* packed = nullptr;
-    TIDAS_CUDA(cudaMallocAsync((void**)&packed, band_pack_bytes(nz, nx, nf), st));
-    tidas_band_pack_kernel<<<(unsigned)images, 256, 0, st>>>((const __nv_bfloat16*)in, packed, nz,
-                                                             nx, nf, nm, nq);
-    rc = check_launch("tidas_band_pack_kernel");
+    if (rc == TIDAS_OK) {
+        cudaError_t e = cudaMallocAsync((void**)&packed, band_pack_bytes(nz, nx, nf), st);
+        if (e != cudaSuccess) {
+            rc = check_cuda(e, "cudaMallocAsync(varying GEMM operands)");
+            packed = nullptr;
+        }
+    }
+    if (rc == TIDAS_OK) {
+        tidas_band_pack_kernel<<<(unsigned)images, 256, 0, st>>>((const __nv_bfloat16*)in, packed,
+                                                                 nz, nx, nf, nm, nq);
+        rc = check_launch("tidas_band_pack_kernel");
+    }
     if (rc == TIDAS_OK) {
         const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
         const int items = nz * ntiles * ((nm + vgem::kMaxFT - 1) / vgem::kMaxFT);
@@ -1218,11 +1287,12 @@ int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int n
                         "cudaFuncSetAttribute(tidas_varying_gemm_kernel)");
         if (rc == TIDAS_OK) {
             tidas_varying_gemm_kernel<<<grid, vgem::kThreads, vgem::kSmem, st>>>(
-                packed, map_out, kern, ld, kz, taps, nz, nx, nf);
+                packed, map_out, map_k, boxw, kz, taps, nz, nx, nf);
             rc = check_launch("tidas_varying_gemm_kernel");
         }
     }
-    cudaFreeAsync(packed, st);
+    if (packed) cudaFreeAsync(packed, st);
+    if (kpad) cudaFreeAsync(kpad, st);
     return rc;
 }
 

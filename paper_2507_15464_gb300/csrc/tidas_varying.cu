@@ -139,7 +139,8 @@ int varying_args(const char* who, const float* kern, int ld, int kz, int taps, i
     if (variant == TIDAS_VARIANT_GEMM_BF16 && gemm_ok) {
         if (nx % 8 != 0)
             return set_error(TIDAS_ERR_UNSUPPORTED, "%s: the GEMM variant needs nx %% 8 == 0", who);
-        TIDAS_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0,
+        TIDAS_REQUIRE(((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0 &&
+                          ((uintptr_t)kern % 16) == 0,
                       "%s: the GEMM variant needs 16-byte aligned arrays", who);
         return 0;
     }

@@ -1,6 +1,7 @@
-"""Learned tiDAS kernel generator: a 4-layer MLP (4 -> 256 -> 256 -> 256 -> 63)
-mapping (lateral x, depth z, receive f-number, transmit angle) to the
-normalised row kernel, trained on exact single-scatterer PSFs.
+"""Learned tiDAS kernel generator: a 4-layer MLP (4 -> 256 -> 256 -> 256 -> 63,
+or -> kz x 63 for band kernels) mapping (lateral x, depth z, receive
+f-number, transmit angle) to the normalised row kernel (or the kz-row band
+patch of the same PSF), trained on exact single-scatterer PSFs.
 
 The paper's conclusion names learned scaling parameters as the way forward;
 the network extends that to the whole kernel and to any (x, F#, angle).
@@ -26,27 +27,36 @@ from . import capi
 from .ops import _ptr, _stream
 
 TAPS = 63
-OUT = 64     # padded output width (column 63 unused, its weights stay zero)
+SLOT = 64    # output columns per kernel row (column 63 of each row is padding)
+OUT = SLOT   # padded output width of the row-kernel network
 IN = 64      # padded input width (4 features)
 HID = 256
-LAYERS = [(HID, IN), (HID, HID), (HID, HID), (OUT, HID)]  # (out, in) per linear layer
+
+
+def layers(kz=1):
+    """(out, in) of the four linear layers; the output holds kz rows of SLOT."""
+    return [(HID, IN), (HID, HID), (HID, HID), (kz * SLOT, HID)]
+
+
+LAYERS = layers(1)
 BOUNDS_LO = (-19.2e-3, 5e-3, 1.0, -math.radians(15.0))
 BOUNDS_HI = (19.2e-3, 60e-3, 3.0, math.radians(15.0))
 
 
-def init_params(seed=5):
+def init_params(seed=5, kz=1):
     """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases (seeded,
     drawn on the host by the shared generator module)."""
     from tidas_workloads import generators
     params = []
-    for li, (o, i) in enumerate(LAYERS):
+    lay = layers(kz)
+    for li, (o, i) in enumerate(lay):
         fan_in = 4 if li == 0 else i
         bound = 1.0 / math.sqrt(fan_in)
         w = generators.uniform((o, i), -bound, bound, (seed, li), np.float32)
         if li == 0:
             w[:, 4:] = 0.0  # padded input columns
-        if li == len(LAYERS) - 1:
-            w[TAPS:, :] = 0.0  # padded output row
+        if li == len(lay) - 1:
+            w.reshape(kz, SLOT, i)[:, TAPS:, :] = 0.0  # padding column of each kernel row
         params.append((w, np.zeros(o, np.float32)))
     return params
 
@@ -60,14 +70,22 @@ def _f32(shape):
 
 
 class KernelMLP:
-    """The kernel generator 4 -> 256 -> 256 -> 256 -> 63 (ReLU between layers):
-    FP32 master weights with BF16 copies for the tensor cores, AdamW training
-    (fit), fused inference (infer) and the layer-by-layer reference path
-    (infer_layers).  `params` is a list of (W [out, in], b [out]) float32 arrays,
-    seeded by init_params() when omitted."""
+    """The kernel generator 4 -> 256 -> 256 -> 256 -> kz x 63 (ReLU between
+    layers; kz = 1: the row kernel): FP32 master weights with BF16 copies for
+    the tensor cores, AdamW training (fit), inference (infer: one fused launch
+    for row kernels, the layer path for band kernels) and the layer-by-layer
+    path (infer_layers).  The output row of a sample holds kz kernel rows of
+    SLOT columns (the layout [kz][SLOT] of the varying tiDAS calls).
+    `params` is a list of (W [out, in], b [out]) float32 arrays, seeded by
+    init_params() when omitted."""
 
-    def __init__(self, params=None, batch=256):
-        params = params or init_params()
+    def __init__(self, params=None, batch=256, kz=1):
+        params = params or init_params(kz=kz)
+        self.kz = kz
+        self.out = kz * SLOT
+        # loss columns: the 63 taps of a row kernel; every column of a band
+        # patch (the padding columns' targets are zero)
+        self.used = TAPS if kz == 1 else self.out
         self.B = batch
         self.W, self.b, self.W16, self.W16t, self.mW, self.vW, self.mb, self.vb = ([] for _ in range(8))
         for (w, b) in params:
@@ -100,8 +118,9 @@ class KernelMLP:
         self.h32 = [_f32((B, HID)) for _ in range(3)]
         self.h16 = [_bf16((B, HID)) for _ in range(3)]
         self.h16t = [_bf16((HID, B)) for _ in range(3)]
-        self.y32 = _f32((B, OUT))
-        self.dy32, self.dy16, self.dy16t = _f32((B, OUT)), _bf16((B, OUT)), _bf16((OUT, B))
+        O = self.out
+        self.y32 = _f32((B, O))
+        self.dy32, self.dy16, self.dy16t = _f32((B, O)), _bf16((B, O)), _bf16((O, B))
         self.dh32 = _f32((B, HID))
         self.dz32 = [_f32((B, HID)) for _ in range(3)]
         self.dz16 = [_bf16((B, HID)) for _ in range(3)]
@@ -109,7 +128,7 @@ class KernelMLP:
         self.gW = [torch.empty_like(W) for W in self.W]
         self.gb = [torch.empty_like(b) for b in self.b]
         self.loss = torch.zeros((), dtype=torch.float64, device="cuda")
-        self.tgt = _f32((B, OUT))
+        self.tgt = _f32((B, O))
 
     # ------------------------------------------------------------ primitives
     def encode(self, samples, out16):
@@ -135,16 +154,17 @@ class KernelMLP:
             self.gemm(a, self.W16[l], M, HID, a.shape[1], self.b[l], True,
                       h32[l] if h32 is not None else None, h16[l], HID)
             a = h16[l]
-        self.gemm(a, self.W16[3], M, OUT, HID, self.b[3], False, y32, None, OUT)
+        self.gemm(a, self.W16[3], M, self.out, HID, self.b[3], False, y32, None, self.out)
 
     # --------------------------------------------------------------- training
     def train_step(self, x16, target, lr, wd=1e-4):
-        """One AdamW step on a mini-batch (x16 [B, 64] BF16, target [B, 64] FP32).
+        """One AdamW step on a mini-batch (x16 [B, 64] BF16, target [B, out] FP32).
         Returns nothing; the batch loss is left in self.loss (device)."""
         B = self.B
+        OUT = self.out
         st = _stream()
         self.forward_into(x16, B, self.h32, self.h16, self.y32)
-        capi.call("tidas_mse", _ptr(self.y32), _ptr(target), B, TAPS, OUT, OUT, _ptr(self.dy32),
+        capi.call("tidas_mse", _ptr(self.y32), _ptr(target), B, self.used, OUT, OUT, _ptr(self.dy32),
                   _ptr(self.loss), st)
         # output layer
         capi.call("tidas_relu_backward", _ptr(self.dy32), None, B * OUT, None, _ptr(self.dy16), st)
@@ -186,7 +206,7 @@ class KernelMLP:
         n = x16_all.shape[0]
         steps_per_epoch = n // self.B
         total = (total_epochs or epochs) * steps_per_epoch
-        xb, tb = _bf16((self.B, IN)), _f32((self.B, OUT))
+        xb, tb = _bf16((self.B, IN)), _f32((self.B, self.out))
         losses = []
         k = first_epoch * steps_per_epoch
         for e in range(first_epoch, epochs):
@@ -195,7 +215,7 @@ class KernelMLP:
                 idx = perm[s * self.B:(s + 1) * self.B]
                 capi.call("tidas_gather_rows", _ptr(x16_all), _ptr(idx), self.B, IN * 2, _ptr(xb),
                           _stream())
-                capi.call("tidas_gather_rows", _ptr(targets_all), _ptr(idx), self.B, OUT * 4,
+                capi.call("tidas_gather_rows", _ptr(targets_all), _ptr(idx), self.B, self.out * 4,
                           _ptr(tb), _stream())
                 lr = 0.5 * lr0 * (1.0 + math.cos(math.pi * k / total))
                 self.train_step(xb, tb, lr)
@@ -209,7 +229,7 @@ class KernelMLP:
         """Write the FP32 master weights and biases, the Adam moments and the
         step count to an .npz file: all the state a resumed run needs (the
         BF16 copies are rebuilt from the masters on load)."""
-        arrays = {"step": np.array(self.step_count, np.int64)}
+        arrays = {"step": np.array(self.step_count, np.int64), "kz": np.array(self.kz, np.int64)}
         for l in range(len(self.W)):
             for name, lst in (("W", self.W), ("b", self.b), ("mW", self.mW), ("vW", self.vW),
                               ("mb", self.mb), ("vb", self.vb)):
@@ -223,7 +243,7 @@ class KernelMLP:
         with np.load(path) as z:
             nl = len(LAYERS)
             params = [(z["W%d" % l], z["b%d" % l]) for l in range(nl)]
-            net = cls(params, batch=batch)
+            net = cls(params, batch=batch, kz=int(z["kz"]) if "kz" in z else 1)
             for l in range(nl):
                 for name, lst in (("mW", net.mW), ("vW", net.vW), ("mb", net.mb), ("vb", net.vb)):
                     lst[l].copy_(torch.from_numpy(z["%s%d" % (name, l)]))
@@ -232,8 +252,11 @@ class KernelMLP:
 
     # -------------------------------------------------------------- inference
     def infer(self, plan, samples, chunk=None):
-        """Kernels [n, 64] (63 used) for samples [n, 4] float64 on the GPU: one
-        fused launch (encode, four BF16 layers, scale by the apodization sum)."""
+        """Kernels [n, out] (63 taps per row of SLOT) for samples [n, 4] float64
+        on the GPU.  Row kernels: one fused launch (encode, four BF16 layers,
+        scale by the apodization sum); band kernels: the layer path."""
+        if self.kz != 1:
+            return self.infer_layers(plan, samples)
         n = samples.shape[0]
         out = _f32((n, OUT))
         scale = _f32((n,))
@@ -250,7 +273,7 @@ class KernelMLP:
         """The same kernels through the layer-by-layer GEMM (tidas_gemm_bf16):
         the reference path of the fused kernel."""
         n = samples.shape[0]
-        out = _f32((n, OUT))
+        out = _f32((n, self.out))
         scale = _f32((n,))
         capi.call("tidas_apod_sum", plan.handle, _ptr(samples), n, _ptr(scale), _stream())
         c = min(chunk, n)
@@ -260,29 +283,34 @@ class KernelMLP:
             m = min(chunk, n - s0)
             self.encode(samples[s0:s0 + m], x16[:m])
             self.forward_into(x16[:m], m, None, [h[:m] for h in h16], out[s0:s0 + m])
-        capi.call("tidas_row_scale", _ptr(out), OUT, _ptr(scale), n, TAPS, _ptr(out), OUT,
-                  _stream())
+        capi.call("tidas_row_scale", _ptr(out), self.out, _ptr(scale), n, self.used, _ptr(out),
+                  self.out, _stream())
         return out
 
 
-def exact_kernels(plan, samples, normalise=False):
-    """Exact PSF rows [n, 64] for samples [n, 4] (float64, CUDA)."""
+def exact_kernels(plan, samples, normalise=False, kz=1):
+    """Exact PSF rows [n, 64] (kz = 1) or band patches [n, kz * 64] (rows of
+    SLOT columns) for samples [n, 4] (float64, CUDA)."""
     n = samples.shape[0]
-    out = _f32((n, OUT))
+    out = _f32((n, kz * SLOT))
     norm = _f32((n,)) if normalise else None
-    capi.call("tidas_psf_batch", plan.handle, _ptr(samples), n, TAPS, _ptr(out), OUT,
-              _ptr(norm) if norm is not None else None, _stream())
+    if kz == 1:
+        capi.call("tidas_psf_batch", plan.handle, _ptr(samples), n, TAPS, _ptr(out), OUT,
+                  _ptr(norm) if norm is not None else None, _stream())
+    else:
+        capi.call("tidas_psf_batch_2d", plan.handle, _ptr(samples), n, kz, TAPS, SLOT, _ptr(out),
+                  kz * SLOT, _ptr(norm) if norm is not None else None, _stream())
     return (out, norm) if normalise else out
 
 
-def training_set(plan, n=20000, seed=4):
-    """(samples, encoded inputs, normalised exact targets) for n uniform draws
-    of (x, z, F#, angle) over the generator's domain."""
+def training_set(plan, n=20000, seed=4, kz=1):
+    """(samples, normalised exact targets) for n uniform draws of (x, z, F#,
+    angle) over the generator's domain; band patches of kz rows for kz > 1."""
     from tidas_workloads import generators
     lo, hi = np.array(BOUNDS_LO), np.array(BOUNDS_HI)
     u = generators.uniform((n, 4), 0.0, 1.0, (seed,), np.float64)
     s = torch.from_numpy(lo + u * (hi - lo)).cuda()
-    tgt, _ = exact_kernels(plan, s, normalise=True)
+    tgt, _ = exact_kernels(plan, s, normalise=True, kz=kz)
     return s, tgt
 
 

@@ -256,34 +256,36 @@ def tidas_adjoint_2d(kernels, img, variant=capi.VARIANT_DIRECT, out=None, worksp
     return _tidas2d(capi.tidas_adjoint_2d, kernels, img, variant, out, workspace)
 
 
-def _varying(fn, kernels, x, variant, out=None):
+def _varying(fn, kernels, x, variant, out=None, taps=None):
     if kernels.dim() == 3:
-        nz, nx, taps = kernels.shape
+        nz, nx, ld = kernels.shape
         kz = 1
     else:
-        nz, nx, kz, taps = kernels.shape
+        nz, nx, kz, ld = kernels.shape
+    taps = ld if taps is None else taps
     nf = x.shape[0]
     _need(kernels, torch.float32, tuple(kernels.shape), "kernels")
     want = torch.bfloat16 if variant == capi.VARIANT_GEMM_BF16 else torch.float32
     _need(x, want, (nf, nz, nx), "input")
     out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
                                                   device=x.device)
-    fn(_ptr(kernels), taps, kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
+    fn(_ptr(kernels), ld, kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
     return out
 
 
-def tidas_forward_varying(kernels, refl, variant=capi.VARIANT_DIRECT, out=None):
+def tidas_forward_varying(kernels, refl, variant=capi.VARIANT_DIRECT, out=None, taps=None):
     """Eq. (2.13) with a kernel per pixel (each pixel adds its own
     single-scatterer image): kernels [nz, nx, taps] (row form) or
     [nz, nx, kz, taps] (band form), refl [B, nz, nx] -> img [B, nz, nx].
     VARIANT_DIRECT: FP32 refl on CUDA cores; VARIANT_GEMM_BF16: BF16 refl on
-    the tcgen05 tensor cores."""
-    return _varying(capi.tidas_forward_varying_2d, kernels, refl, variant, out)
+    the tcgen05 tensor cores.  The last kernel axis is the row pitch; taps
+    (default: all of it) are the columns in use."""
+    return _varying(capi.tidas_forward_varying_2d, kernels, refl, variant, out, taps)
 
 
-def tidas_adjoint_varying(kernels, img, variant=capi.VARIANT_DIRECT, out=None):
+def tidas_adjoint_varying(kernels, img, variant=capi.VARIANT_DIRECT, out=None, taps=None):
     """Transpose of tidas_forward_varying: img [B, nz, nx] -> refl [B, nz, nx]."""
-    return _varying(capi.tidas_adjoint_varying_2d, kernels, img, variant, out)
+    return _varying(capi.tidas_adjoint_varying_2d, kernels, img, variant, out, taps)
 
 
 class LineExperiment:

@@ -174,6 +174,38 @@ def test_psf_batch_matches_oracle():
         assert np.all(out[i, 63:] == 0)
 
 
+def _oracle_patch(xs, z, fnum, deg, kz, taps=63):
+    # the exact image of a unit scatterer at (xs, z) over kz rows x taps
+    # columns centred on it (rows z + (u - kz/2) dz): Eq. (2.1) then (2.2)
+    import oracle
+    base = presets.geometry("pw128_compound")
+    dx, dz = base["dx"], base["dz"]
+    geom = dict(base, angles_deg=[deg], fnum=fnum, nz=kz, z0=z - (kz // 2) * dz - dz / 2,
+                nx=taps, x0=xs - (taps // 2) * dx - dx / 2)
+    O = oracle.Oracle(geom)
+    return O.das(O.synthesize([[xs, z]], [[1.0, 0.0]]))
+
+
+@pytest.mark.parametrize("kz", [1, 8, 5])
+def test_psf_batch_2d_matches_oracle(kz):
+    # band patches (rows of 64 columns, 63 taps) against the oracle's image of
+    # each scatterer; the centre row is the row PSF of tidas_psf_batch
+    from paper_2507_15464_gb300.ops import DasPlan
+    g = G()
+    P = DasPlan(presets.geometry("pw128_compound"))
+    cases = [(0.0, 20e-3, 1.5, 0.0), (-12.3e-3, 7.1e-3, 1.0, -11.0), (17.9e-3, 55e-3, 2.7, 14.5)]
+    samples = to_dev(np.array([[x, z, f, d * math.pi / 180.0] for x, z, f, d in cases]))
+    out, norm = g.exact_kernels(P, samples, normalise=True, kz=kz)
+    out, norm = host(out).reshape(len(cases), kz, 64), host(norm)
+    rows, norm1 = g.exact_kernels(P, samples, normalise=True)
+    for i, (x, z, f, d) in enumerate(cases):
+        ref = _oracle_patch(x, z, f, d, kz)
+        assert rel_l2(out[i, :, :63] * norm[i], ref) <= 1e-5
+        assert not out[i, :, 63].any()
+        np.testing.assert_array_equal(out[i, kz // 2], host(rows)[i])
+    assert np.array_equal(norm, host(norm1))
+
+
 def _bf16(a):
     return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().double().numpy()
 
@@ -340,3 +372,50 @@ def test_checkpoint_resume_matches_an_uninterrupted_run(tmp_path):
     # and the restored network infers like the original
     smp = torch.from_numpy(np.array([[1e-3, 20e-3, 1.5, 0.05], [-5e-3, 40e-3, 2.5, -0.1]])).cuda()
     assert torch.equal(a.infer(P, smp), c.infer(P, smp))
+
+
+def test_learned_band_kernels_improve_images_over_fixed_band_kernels():
+    # the generator trained on 8 x 63 band patches of exact PSFs, applied per
+    # pixel on the tensor cores (varying band GEMM, exact kernels where the
+    # learned ones are more than 2 % off), against exact single-angle DAS on
+    # a 64-row slab of the grid under the unseen geometry; beside it plain
+    # tiDAS with fixed band kernels (fitted at the centre column), the exact
+    # per-pixel band kernels (what 8 x 63 kernels can do at best) and row
+    # kernels
+    from paper_2507_15464_gb300 import capi, ops
+    from paper_2507_15464_gb300.ops import DasPlan, _ptr
+    g = G()
+    kz = 8
+    geom = presets.geometry("pw128_compound")
+    P = DasPlan(geom)
+    s, tgt = g.training_set(P, n=20000, seed=4, kz=kz)
+    net = g.KernelMLP(batch=256, kz=kz)
+    x16 = torch.empty((20000, 64), dtype=torch.bfloat16, device="cuda")
+    net.encode(s, x16)
+    net.fit(x16, tgt, 200, _perms(200, 20000, 5), lr0=1e-3)
+    fnum, ang = 1.7, 7.5
+    sub = dict(geom, nz=64, z0=geom["z0"] + 400 * geom["dz"])
+    smp = g.grid_samples(sub, fnum, ang * math.pi / 180.0)
+    npix = smp.shape[0]
+    learned = net.infer(P, smp)
+    exact = g.exact_kernels(P, smp, kz=kz)
+    mixed = torch.empty_like(learned)
+    capi.call("tidas_kernel_fallback", _ptr(learned), net.out, _ptr(exact), net.out, npix,
+              net.out, 0.02, _ptr(mixed), net.out, None, 0)
+    P1 = DasPlan(dict(sub, angles_deg=[ang], fnum=fnum))
+    refl = to_dev(generators.bernoulli_normal((1, 64, 512), 0.02, (85,)))
+    das = host(P1.forward(P1.synthesize_grid(refl)))[0]
+
+    def nr(y):
+        return rel_l2(host(y)[0], das)
+
+    shape = (64, 512, kz, g.SLOT)
+    e_l = nr(ops.tidas_forward_varying(mixed.view(shape), refl.to(torch.bfloat16),
+                                       variant=capi.VARIANT_GEMM_BF16, taps=63))
+    e_x = nr(ops.tidas_forward_varying(exact.view(shape), refl, taps=63))
+    e_b = nr(ops.tidas_forward_2d(P1.fit_kernels_2d(kz, 63), refl))
+    e_r = nr(ops.tidas_forward(P1.fit_kernels(63)[0], refl))
+    msg = "learned %.3f exact-varying %.3f fixed-band %.3f rows %.3f" % (e_l, e_x, e_b, e_r)
+    assert e_l <= 1.1 * e_x + 0.01, msg
+    assert e_l <= 0.85 * e_b, msg
+    assert e_l <= 0.5 * e_r, msg

@@ -138,6 +138,12 @@ def test_varying_gemm_matches_oracle(nf, nz, nx, kz, taps):
     # and close to the FP32 direct path on every frame
     yd = host(o.tidas_forward_varying(to_dev(k), x16.float()))
     assert rel_l2(y, yd) <= 5e-3
+    # kernels at a 64-column pitch (read in place by the tensor copies) with
+    # garbage in the columns past the taps: the same image
+    kp = np.full(k.shape[:-1] + (64,), 1e3, np.float32)
+    kp[..., :taps] = k
+    yp = host(o.tidas_forward_varying(to_dev(kp), x16, variant=capi.VARIANT_GEMM_BF16, taps=taps))
+    np.testing.assert_array_equal(yp, y)
 
 
 def test_varying_gemm_full_width_band_slab():
