@@ -341,14 +341,28 @@ def run_ours(args):
     # capture of the current kernel (dram__bytes_read + dram__bytes_write);
     # None whenever the kernel changes after that capture
     traffic = 694.3e6 if BATCH == 64 else None
+    # DRAM bytes of the step's two launches from the same capture: the repack
+    # reads the batch and writes its staged copy, the DAS kernel reads that copy
+    # (L2 serves the re-reads of neighbouring tiles) and writes the image
+    step_traffic = {"das_tc_pack_kernel": 1451.1e6, "das_tc_kernel": 694.3e6} \
+        if BATCH == 64 else None
     roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
             "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
             "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x 2070 MHz" % sms,
             "work": "%.4g updates x 10 flop (cubic taps + apodization)" % updates,
             "g_updates_s": updates / (ms * 1e-3) / 1e9,
             "timed": "whole step (das_tc_pack_kernel + das_tc_kernel)",
-            "note": "issue-bound: 71 % of issue slots busy, mostly the weight-building "
-                    "warps; tensor pipe 5.1 % busy (ncu)"}
+            "step_traffic": step_traffic,
+            "step_traffic_over_algorithmic": (sum(step_traffic.values()) / alg_bytes
+                                              if step_traffic else None),
+            "hw_counters": {"issue_active": 0.711, "tensor_pipe_active": 0.051,
+                            "lts_throughput": 0.041,
+                            "warp_instructions_per_pair": 1030,
+                            "source": "ncu, profiles/das_tc_kernel_pw128_compound_64frames_f16.md"},
+            "note": "instruction-issue-bound: 71 % of issue slots busy, mostly the "
+                    "weight-building warps; tensor pipe 5.1 % busy.  The frac above is "
+                    "the algorithmic flops (10 per update) over a derived CUDA-core FP32 "
+                    "peak; the hardware counters are the bound"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     hbm = {"achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
            "peak_source": peak_src, "bytes_per_launch": alg_bytes}
