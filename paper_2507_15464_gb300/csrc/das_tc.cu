@@ -280,6 +280,7 @@ __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __res
     }
 }
 
+template <int INTERP>
 __global__ void __launch_bounds__(dtc::kThreads, 2)
     das_tc_kernel(const __half* __restrict__ packed, DasDev d, const int* __restrict__ tab,
                   const int2* __restrict__ range, int tiles_x, int nf, int NF, int C,
@@ -488,18 +489,31 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         const float zs = __ldg(d.zs + izc);
         uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
         const int swz = m & 7;
-        float w = 0.f, exc = 0.f;
-        // columns this thread last wrote into the group's two tiles, one byte
-        // per pair of the round that wrote them (0xff: none); tile j & 1 in
-        // bits 16 (j & 1) .. 16 (j & 1) + 15
-        uint32_t prev = 0xffffffffu;
+        float exc = 0.f;
+        // apodized interpolation weights of element n as polynomials in the
+        // fraction phi, with the Hann weight w folded into the coefficients
+        // (Horner form): cubic Keys, w w0 = phi (phi (ca phi + cw) + ca),
+        // w w1 = phi^2 (cc phi + cd) + cw, w w2 = phi (phi (cf - cc phi) + ch),
+        // w w3 = phi^2 (ch phi - ch); linear w (1 - phi), w phi
+        float cw = 0.f, ca = 0.f, cc = 0.f, cd = 0.f, cf = 0.f, ch = 0.f;
+        auto set_weight = [&](float w) {
+            cw = w;
+            ca = -0.5f * w;
+            cc = 1.5f * w;
+            cd = -2.5f * w;
+            cf = 2.f * w;
+            ch = 0.5f * w;
+        };
+        // the column of the first tap this thread wrote into each of the
+        // group's two tiles, per pair of the round that wrote it (-1: none):
+        // r0 / r1 for the tile of the current round, o0 / o1 for the other
+        int r0 = -1, r1 = -1, o0 = -1, o1 = -1;
         int n = n_lo, a = 0;  // at the top of a round: its first pair is (element n, angle a)
-        // apodization and receive excess of element n; the lateral offset of
-        // element n + 1 is loaded one element ahead
+        // the lateral offset of element n + 1 is loaded one element ahead
         float dxs_next = 0.f;
         if (npairs > 0) {
             const float dxs = __ldg(d.dxs + (size_t)n * d.nx + ixc);
-            w = valid ? builder_apod(dxs, zs, d.fnum) : 0.f;
+            set_weight(valid ? builder_apod(dxs, zs, d.fnum) : 0.f);
             exc = rx_excess(dxs, zs);
             if (n + 1 <= n_hi) dxs_next = __ldg(d.dxs + (size_t)(n + 1) * d.nx + ixc);
         }
@@ -512,19 +526,20 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             // MMA warp saw complete before the previous group barrier
             {
                 uint8_t* W = rowp + (grp + kGroups * (j & 1)) * kWBytes;
-                const int shj = 16 * (j & 1);
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    const int pc = (int)(int8_t)(prev >> (shj + 8 * p));
-                    if (pc >= 0) {
-                        *reinterpret_cast<uint4*>(W + (((pc >> 3) ^ swz) << 4)) =
+                if (r0 >= 0) {
+                    *reinterpret_cast<uint4*>(W + (((r0 >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+                    if ((r0 & 7) > 4)
+                        *reinterpret_cast<uint4*>(W + ((((r0 >> 3) + 1) ^ swz) << 4)) =
                             make_uint4(0, 0, 0, 0);
-                        if ((pc & 7) > 4)
-                            *reinterpret_cast<uint4*>(W + ((((pc >> 3) + 1) ^ swz) << 4)) =
-                                make_uint4(0, 0, 0, 0);
-                    }
                 }
-                int nc0 = -1, nc1 = -1;
+                if (r1 >= 0) {
+                    *reinterpret_cast<uint4*>(W + (((r1 >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+                    if ((r1 & 7) > 4)
+                        *reinterpret_cast<uint4*>(W + ((((r1 >> 3) + 1) ^ swz) << 4)) =
+                            make_uint4(0, 0, 0, 0);
+                }
+                r0 = -1;
+                r1 = -1;
                 int col0 = 0;  // first column of the pair in the weight tile
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
@@ -540,34 +555,38 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                         const float dxs =
                             dn == 1 ? dxs_next : __ldg(d.dxs + (size_t)n * d.nx + ixc);
                         if (n + 1 <= n_hi) dxs_next = __ldg(d.dxs + (size_t)(n + 1) * d.nx + ixc);
-                        w = valid ? builder_apod(dxs, zs, d.fnum) : 0.f;
+                        set_weight(valid ? builder_apod(dxs, zs, d.fnum) : 0.f);
                         exc = rx_excess(dxs, zs);
                     }
                     const int e = s_tab[q + p];
                     const int k0 = entry_k0(e), steps = e & 7;
-                    if (w != 0.f) {
+                    if (cw != 0.f) {
                         const int2 bs = s_base[a * kM + m];
                         const float uf = __int_as_float(bs.y) + exc;
                         const float fl = floorf(uf);
                         const float phi = uf - fl;
                         const int i = bs.x + (int)fl;
-                        float v[4];
+                        float v0, v1, v2, v3;
                         int c;
-                        if (d.interp == TIDAS_INTERP_CUBIC) {
-                            keys_weights(phi, v[0], v[1], v[2], v[3]);
+                        if (INTERP == TIDAS_INTERP_CUBIC) {
+                            const float p2 = phi * phi;
+                            v0 = fmaf(fmaf(ca, phi, cw), phi, ca) * phi;
+                            v1 = fmaf(fmaf(cc, phi, cd), p2, cw);
+                            v2 = fmaf(fmaf(-cc, phi, cf), phi, ch) * phi;
+                            v3 = fmaf(ch, phi, -ch) * p2;
                             c = i - 1 - k0;
                         } else {
-                            v[0] = 1.f - phi;
-                            v[1] = phi;
-                            v[2] = 0.f;
-                            v[3] = 0.f;
+                            v0 = fmaf(-cw, phi, cw);
+                            v1 = cw * phi;
+                            v2 = 0.f;
+                            v3 = 0.f;
                             c = i - k0;
                         }
                         // inside the pair's window by the table's construction,
                         // unless the window misses the record (steps 0)
                         if (c >= 0 && c + 3 < steps * kKC) {
-                            const __half2 h01 = __floats2half2_rn(w * v[0], w * v[1]);
-                            const __half2 h23 = __floats2half2_rn(w * v[2], w * v[3]);
+                            const __half2 h01 = __floats2half2_rn(v0, v1);
+                            const __half2 h23 = __floats2half2_rn(v2, v3);
                             const uint64_t pk =
                                 (uint64_t)*reinterpret_cast<const uint32_t*>(&h01) |
                                 ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
@@ -578,15 +597,19 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                             if ((c & 7) > 4)
                                 *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
                             if (p)
-                                nc1 = c;
+                                r1 = c;
                             else
-                                nc0 = c;
+                                r0 = c;
                         }
                     }
                     col0 += steps * kKC;
                 }
-                prev = (prev & ~(0xffffu << shj)) |
-                       ((uint32_t)((nc0 & 0xff) | ((nc1 & 0xff) << 8)) << shj);
+                // the next round writes the other tile
+                const int t0 = r0, t1 = r1;
+                r0 = o0;
+                r1 = o1;
+                o0 = t0;
+                o1 = t1;
             }
             fence_proxy_async_smem();
             if (group_bar(grp, *s_abort)) break;
@@ -746,10 +769,18 @@ int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_
     int rc = check_launch("das_tc_pack_kernel");
     if (rc) return rc;
     const size_t smem = smem_bytes(NF, C, A, NE);
-    TIDAS_CUDA(cudaFuncSetAttribute(das_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(P.tc_tiles, FT);
-    das_tc_kernel<<<grid, kThreads, smem, st>>>(packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf,
-                                                NF, C, img);
+    if (d.interp == TIDAS_INTERP_CUBIC) {
+        TIDAS_CUDA(cudaFuncSetAttribute(das_tc_kernel<TIDAS_INTERP_CUBIC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        das_tc_kernel<TIDAS_INTERP_CUBIC><<<grid, kThreads, smem, st>>>(
+            packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF, C, img);
+    } else {
+        TIDAS_CUDA(cudaFuncSetAttribute(das_tc_kernel<TIDAS_INTERP_LINEAR>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        das_tc_kernel<TIDAS_INTERP_LINEAR><<<grid, kThreads, smem, st>>>(
+            packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF, C, img);
+    }
     return check_launch("das_tc_kernel");
 }
 
