@@ -1197,7 +1197,61 @@ def bench_learned_band(torch, capi, generators, epochs, kz=8, frames=256):
     res["image_nrmse_vs_exact_das"] = {"learned_band_varying": nr(y_l),
                                        "exact_band_varying": nr(y_e),
                                        "fixed_band": nr(y_b), "fixed_rows": nr(y_r)}
+    del mixed, exact, km, ke, out
+    res["compound"] = learned_band_compound(torch, capi, gen, ops, net, P, geom, refl, kz)
     return res
+
+
+def learned_band_compound(torch, capi, gen, ops, net, P, geom, refl, kz, z_row=400, rows=128):
+    """The compounded workload itself (11 plane waves, F# 1.5) on a slab of
+    rows: DAS is linear in the transmit events, so a pixel's compound kernel
+    is the sum of its single-angle kernels.  Learned kernels (as inferred,
+    and with exact ones where more than 2 % off), exact ones, the fixed band
+    kernels of plain tiDAS and row kernels, against exact compound DAS."""
+    import math
+    from paper_2507_15464_gb300.ops import DasPlan, _ptr, _stream
+    sub = dict(geom, nz=rows, z0=geom["z0"] + z_row * geom["dz"])
+    Ps = DasPlan(sub)
+    npix = rows * sub["nx"]
+    kl = torch.zeros((npix, net.out), device="cuda")
+    km = torch.zeros_like(kl)
+    kx = torch.zeros_like(kl)
+    ma = torch.empty_like(kl)
+    stream = torch.cuda.current_stream()
+    t_inf = 0.0
+    for deg in geom["angles_deg"]:
+        smp = gen.grid_samples(sub, geom["fnum"], math.radians(deg))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        la = net.infer(P, smp)
+        e1.record(stream)
+        ea = gen.exact_kernels(P, smp, kz=kz)
+        capi.call("tidas_kernel_fallback", _ptr(la), net.out, _ptr(ea), net.out, npix, net.out,
+                  0.02, _ptr(ma), net.out, None, _stream())
+        torch.cuda.synchronize()
+        t_inf += e0.elapsed_time(e1)
+        kl += la
+        km += ma
+        kx += ea
+    r = refl[:1, z_row:z_row + rows].contiguous()
+    das = Ps.forward(Ps.synthesize_grid(r))[0].double()
+
+    def nr(y):
+        return float((y[0].double() - das).norm() / das.norm())
+
+    shape = (rows, sub["nx"], kz, gen.SLOT)
+    rb = r.to(torch.bfloat16)
+    return {"slab": "rows %d..%d (z %.1f-%.1f mm), 512 columns, 11 angles, F# 1.5"
+                    % (z_row, z_row + rows - 1, 1e3 * sub["z0"], 1e3 * (sub["z0"] + rows * sub["dz"])),
+            "inference_ms_per_angle_per_slab": t_inf / len(geom["angles_deg"]),
+            "image_nrmse_vs_exact_das": {
+                "learned_band_varying": nr(ops.tidas_forward_varying(
+                    kl.view(shape), rb, variant=capi.VARIANT_GEMM_BF16, taps=TAPS)),
+                "learned_band_varying_with_fallback": nr(ops.tidas_forward_varying(
+                    km.view(shape), rb, variant=capi.VARIANT_GEMM_BF16, taps=TAPS)),
+                "exact_band_varying": nr(ops.tidas_forward_varying(kx.view(shape), r, taps=TAPS)),
+                "fixed_band": nr(ops.tidas_forward_2d(Ps.fit_kernels_2d(kz, TAPS), r)),
+                "fixed_rows": nr(ops.tidas_forward(Ps.fit_kernels(TAPS)[0], r))}}
 
 
 # ------------------------------------------------------ reference arm

@@ -419,3 +419,26 @@ def test_learned_band_kernels_improve_images_over_fixed_band_kernels():
     assert e_l <= 1.1 * e_x + 0.01, msg
     assert e_l <= 0.85 * e_b, msg
     assert e_l <= 0.5 * e_r, msg
+    # the compounded acquisition (11 plane waves, F# 1.5): DAS is linear in
+    # the transmit events, so a pixel's kernel is the sum of its single-angle
+    # kernels; the network's own kernels (no fallback) against exact compound
+    # DAS, beside the exact per-pixel kernels and the fixed band kernels
+    Pc = DasPlan(sub)
+    kl = torch.zeros((npix, net.out), device="cuda")
+    kx = torch.zeros_like(kl)
+    for deg in geom["angles_deg"]:
+        sa = g.grid_samples(sub, geom["fnum"], deg * math.pi / 180.0)
+        kl += net.infer(P, sa)
+        kx += g.exact_kernels(P, sa, kz=kz)
+    dasc = host(Pc.forward(Pc.synthesize_grid(refl)))[0]
+
+    def nrc(y):
+        return rel_l2(host(y)[0], dasc)
+
+    c_l = nrc(ops.tidas_forward_varying(kl.view(shape), refl.to(torch.bfloat16),
+                                        variant=capi.VARIANT_GEMM_BF16, taps=63))
+    c_x = nrc(ops.tidas_forward_varying(kx.view(shape), refl, taps=63))
+    c_b = nrc(ops.tidas_forward_2d(Pc.fit_kernels_2d(kz, 63), refl))
+    msg = "compound: learned %.3f exact-varying %.3f fixed-band %.3f" % (c_l, c_x, c_b)
+    assert c_l <= 1.1 * c_x + 0.01, msg
+    assert c_l <= 0.6 * c_b, msg
