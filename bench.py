@@ -442,14 +442,19 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     ok_e2e = torch.equal(host_out[(n_e2e - 1) & 1], img.cpu())
     e2e_ms, serial_ms = max_over_ranks(torch, [e2e_ms, serial_ms], world, "cuda")
+    first, count = P16.read_window()
     e2e = {"value": whole_job_mpix_s(BATCH, npx, world, e2e_ms), "unit": "Mpixels/s",
-           "h2d_bytes_per_step": rf.numel() * 2, "d2h_bytes_per_step": img.numel() * 4,
+           "h2d_bytes_per_step": streamer.h2d_bytes, "d2h_bytes_per_step": img.numel() * 4,
            "ms_per_step": e2e_ms, "steps": n_e2e,
            "form": "ops.DasStreamer: copies of neighbouring steps overlap the beamforming; "
                    "the stream's first upload and last read-back are inside the timed region",
+           "upload": "the plan's read window of every record, samples %d..%d of %d "
+                     "(das_upload_window; the samples DAS weights)"
+                     % (first, first + count - 1, g["n_samples"]),
            "image_matches_device_step": bool(ok_e2e),
            "serial": {"value": whole_job_mpix_s(BATCH, npx, world, serial_ms),
-                      "ms_per_step": serial_ms}}
+                      "ms_per_step": serial_ms, "h2d_bytes_per_step": rf.numel() * 2,
+                      "form": "whole-record upload, beamforming and read-back on one stream"}}
 
     # ---- the 64-element single-angle case (DAS, 31-tap fit and apply)
     if rank == 0 and not args.no_config1:

@@ -103,6 +103,24 @@ int das_plan_destroy(das_plan plan);
 #define DAS_OPT_TENSOR_CORES 1
 int das_plan_set_option(das_plan plan, int32_t option, int32_t value);
 
+/* The samples of every channel record that das_forward weights: every
+ * interpolation tap of every pixel (Eq. (2.2) with the plan's delays, Eq.
+ * (2.3)) lies in [*first_sample, *first_sample + *n_samples) (the extreme
+ * delays over the grid, with one sample of margin each side).  Samples
+ * outside the window never change the image as long as they are finite:
+ * they are not read, or (the tensor-core path's aligned windows) multiplied
+ * by exact zeros. */
+int das_plan_read_window(das_plan plan, int32_t* first_sample, int32_t* n_samples);
+
+/* Host -> device copy of the read window of every record of a batch:
+ * rf[f][a][n][k] = host_rf[f][a][n][k] for k in the window, other samples of
+ * rf untouched (keep them finite, e.g. zeroed once).  host_rf is a HOST
+ * pointer [n_frames][n_angles][n_elem][n_samples] of the plan's rf_dtype
+ * (page-locked for the copy to be asynchronous), rf a DEVICE pointer of the
+ * same layout.  One cudaMemcpy2DAsync on `stream`. */
+int das_upload_window(das_plan plan, const void* host_rf, void* rf, int32_t n_frames,
+                      void* stream);
+
 /* Channel data of point scatterers under the Born approximation, Eq. (2.1):
  * rf[f][a][n][k] = sum_j Re(A_fj * p(t_k - tau_a,n(x_fj, z_fj))), with the
  * Gaussian-modulated pulse p (6 dB band f0(1 +- frac_bw/2), truncated at the

@@ -54,6 +54,8 @@ _SIG = {
     "das_plan_create": [ctypes.POINTER(das_params), ctypes.POINTER(ctypes.c_void_p)],
     "das_plan_destroy": [_P],
     "das_plan_set_option": [_P, _I, _I],
+    "das_plan_read_window": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "das_upload_window": [_P, _P, _P, _I, _P],
     "das_synthesize": [_P, _P, _P, _I, _I, _P, _P],
     "das_synthesize_grid": [_P, _P, _P, _I, _P],
     "das_synthesize_adjoint": [_P, _P, _P, _I, _P],
@@ -292,3 +294,9 @@ def tidas_last_error():
 
 def tidas_set_debug_option(option, value):
     return _check(load().tidas_set_debug_option(option, value))
+
+
+def das_plan_read_window(plan):
+    first, count = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().das_plan_read_window(plan, ctypes.byref(first), ctypes.byref(count)))
+    return first.value, count.value

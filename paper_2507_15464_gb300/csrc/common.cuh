@@ -62,6 +62,8 @@ struct Plan {
     void* blob;             // single device allocation holding every table
     const double* d_sncs;   // device [A][2]: sin, cos of each angle (host libm values)
     bool taps_in_range;     // every interpolation tap of every pixel lies in [0, n_samples)
+    int read_first = 0;     // samples [read_first, read_first + read_count) hold every
+    int read_count = 0;     // tap that any pixel weights (das_plan_read_window)
     double thalf_samples, beta_samples, wcar;
     // tensor-core DAS of FP16 plans: per-(tile, angle, element) sample windows
     int* tc_tab = nullptr;

@@ -180,6 +180,12 @@ extern "C" int das_plan_create(const das_params* params, das_plan* out_plan) {
                 }
             }
         P->taps_in_range = (floor(umin) - 2.0 >= 0.0) && (floor(umax) + 3.0 <= p.n_samples - 1.0);
+        // samples any pixel can weight: taps floor(u) - 1 .. floor(u) + 2 of the
+        // extreme delays, one more sample each side for the split-delay rounding
+        const double first = fmax(0.0, floor(umin) - 3.0);
+        const double last = fmin((double)p.n_samples - 1.0, floor(umax) + 4.0);
+        P->read_first = (int)first;
+        P->read_count = last >= first ? (int)(last - first) + 1 : 0;
     }
 
     // one blob, 256-byte aligned pieces
@@ -261,6 +267,30 @@ extern "C" int das_plan_set_option(das_plan plan, int32_t option, int32_t value)
         return TIDAS_OK;
     }
     return set_error(TIDAS_ERR_ARG, "das_plan_set_option: unknown option %d", option);
+}
+
+extern "C" int das_plan_read_window(das_plan plan, int32_t* first_sample, int32_t* n_samples) {
+    TIDAS_REQUIRE(plan && first_sample && n_samples, "das_plan_read_window: null argument");
+    const Plan* P = (const Plan*)plan;
+    *first_sample = P->read_first;
+    *n_samples = P->read_count;
+    return TIDAS_OK;
+}
+
+extern "C" int das_upload_window(das_plan plan, const void* host_rf, void* rf, int32_t n_frames,
+                                 void* stream) {
+    TIDAS_REQUIRE(plan && host_rf && rf, "das_upload_window: null argument");
+    TIDAS_REQUIRE(n_frames >= 1, "das_upload_window: n_frames must be >= 1");
+    const Plan* P = (const Plan*)plan;
+    if (P->read_count == 0) return TIDAS_OK;
+    const size_t es = P->p.rf_dtype == TIDAS_RF_F16 ? 2 : 4;
+    const size_t pitch = (size_t)P->p.n_samples * es;
+    const size_t rows = (size_t)n_frames * P->p.n_angles * P->p.n_elem;
+    const size_t off = (size_t)P->read_first * es;
+    TIDAS_CUDA(cudaMemcpy2DAsync((char*)rf + off, pitch, (const char*)host_rf + off, pitch,
+                                 (size_t)P->read_count * es, rows, cudaMemcpyHostToDevice,
+                                 (cudaStream_t)stream));
+    return TIDAS_OK;
 }
 
 extern "C" int das_plan_destroy(das_plan plan) {

@@ -53,6 +53,11 @@ class DasPlan:
         self.A, self.N, self.S = p.n_angles, p.n_elem, p.n_samples
         self.nx, self.nz = p.nx, p.nz
 
+    def read_window(self):
+        """(first sample, count) of the samples das_forward weights in every
+        channel record; samples outside never change the image if finite."""
+        return capi.das_plan_read_window(self.handle)
+
     def set_tensor_cores(self, on: bool):
         """Route batches of >= 16 FP16 frames to the tensor-core DAS (default) or not."""
         capi.call("das_plan_set_option", self.handle, 1, 1 if on else 0)
@@ -156,15 +161,22 @@ class DasStreamer:
     stream, batch k + 1 is uploaded on an upload stream and batch k - 1's
     image is read back on a download stream.  Every batch still makes its
     own host -> device and device -> host copy; events order the reuse of
-    each buffer.  There is a single compute stream, so the plan's staging
-    buffer serves one batch at a time.  Destroying a plan synchronises the
-    device (cudaFree), which drains the pipeline: keep plan lifetimes (and
-    the garbage collector) out of the submission loop."""
+    each buffer.  The upload copies the plan's read window of every record
+    (das_upload_window: the samples DAS weights); the device buffers are
+    zeroed once, so the samples outside stay finite and the images equal
+    those of whole-record uploads.  There is a single compute stream, so the
+    plan's staging buffer serves one batch at a time.  Destroying a plan
+    synchronises the device (cudaFree), which drains the pipeline: keep plan
+    lifetimes (and the garbage collector) out of the submission loop."""
 
     def __init__(self, plan: DasPlan, n_frames: int, device="cuda"):
         self.plan = plan
-        self.rf = [torch.empty(plan.rf_shape(n_frames), dtype=plan.rf_dtype, device=device)
+        self.n_frames = n_frames
+        self.rf = [torch.zeros(plan.rf_shape(n_frames), dtype=plan.rf_dtype, device=device)
                    for _ in range(2)]
+        first, count = plan.read_window()
+        esize = self.rf[0].element_size()
+        self.h2d_bytes = count * esize * (self.rf[0].numel() // plan.rf_shape(n_frames)[-1])
         self.img = [torch.empty(plan.img_shape(n_frames), dtype=torch.float32, device=device)
                     for _ in range(2)]
         self.up, self.comp, self.down = (torch.cuda.Stream() for _ in range(3))
@@ -182,7 +194,11 @@ class DasStreamer:
         with torch.cuda.stream(self.up):
             if reuse:
                 self.up.wait_event(self.computed[b])  # batch k - 2 has read rf[b]
-            self.rf[b].copy_(host_rf, non_blocking=True)
+            if not host_rf.is_pinned():
+                raise ValueError("DasStreamer needs page-locked host batches")
+            _need(host_rf, self.plan.rf_dtype, self.rf[b].shape, "host_rf")
+            capi.call("das_upload_window", self.plan.handle, host_rf.data_ptr(),
+                      _ptr(self.rf[b]), self.n_frames, self.up.cuda_stream)
             self.uploaded[b].record(self.up)
         with torch.cuda.stream(self.comp):
             self.comp.wait_event(self.uploaded[b])

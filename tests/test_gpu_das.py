@@ -324,3 +324,33 @@ def test_streamer_overlapped_batches_equal_plain_forward():
     torch.cuda.synchronize()
     for b, o in zip(batches, outs):
         np.testing.assert_array_equal(o.numpy(), host(P.forward(b.cuda())))
+
+
+@pytest.mark.parametrize("dtype,nf,big", [("f16", 16, 6.0e4), ("f16", 3, 6.0e4), ("f32", 2, 1e30)])
+def test_read_window_holds_every_weighted_sample(dtype, nf, big):
+    # samples outside the plan's read window, set to huge finite values,
+    # leave the image bit for bit unchanged: on the tensor cores (16 FP16
+    # frames), the frames-innermost path (3 FP16 frames) and the CUDA cores
+    # (FP32); and the windowed upload gives the same image as a full one
+    from paper_2507_15464_gb300 import capi
+    g = presets.geometry("pw128_compound", nz=96, z0=20e-3)
+    tdt = torch.float16 if dtype == "f16" else torch.float32
+    P = plan(g, tdt)
+    first, count = P.read_window()
+    S = g["n_samples"]
+    assert 0 < first and first + count < S  # a strict sub-window for this grid
+    rf = generators.standard_normal(P.rf_shape(nf), (31, nf), np.float32)
+    inside = rf.copy()
+    inside[..., :first] = 0.0
+    inside[..., first + count:] = 0.0
+    outside = rf.copy()
+    outside[..., :first] = big
+    outside[..., first + count:] = -big
+    a = host(P.forward(to_dev(inside, tdt)))
+    b = host(P.forward(to_dev(outside, tdt)))
+    np.testing.assert_array_equal(a, b)
+    host_rf = torch.from_numpy(outside).to(tdt).pin_memory()
+    dev = torch.zeros(P.rf_shape(nf), dtype=tdt, device="cuda")
+    capi.call("das_upload_window", P.handle, host_rf.data_ptr(), dev.data_ptr(), nf,
+              torch.cuda.current_stream().cuda_stream)
+    np.testing.assert_array_equal(host(P.forward(dev)), a)
