@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                   float* __restrict__ img) {
     using namespace dtc;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_align1024(smem_raw);
     const int CB = chunk_bytes(NF);
     const int A = d.n_angles, NE = d.n_elem;
     const int Sp = packed_len(d.n_samples);
@@ -435,7 +435,15 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         uint64_t* gempty = empty + grp * kPairSlots;
         const uint32_t ring = smem_u32(sC + grp * C * CB);
         int pos = 0, j = 0;  // first chunk of round j in the ring
-        bool first = true, bad = false;
+        bool bad = false;
+        uint32_t accf = 0u;  // 0 until the group's first MMA has written its accumulator
+        const uint64_t b0 = desc_mn_chunk(ring, NF);
+        const uint32_t b_lo0 = (uint32_t)b0, b_hi = (uint32_t)(b0 >> 32);
+        const uint32_t b_step = (uint32_t)CB >> 4, b_end = b_lo0 + (uint32_t)C * b_step;
+        const uint64_t w0 = desc_sw128_kmajor(smem_u32(sW + grp * kWBytes));
+        const uint32_t w_lo0 = (uint32_t)w0, w_hi = (uint32_t)(w0 >> 32);
+        const uint32_t w_lo1 =
+            (uint32_t)desc_sw128_kmajor(smem_u32(sW + (grp + kGroups) * kWBytes));
         int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
         for (; q < npairs; q = next_round(s_tab, q, npairs), ++j) {
             // Round j - 1's MMAs must be complete before this barrier: past it the
@@ -454,14 +462,22 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                                                (uint32_t)(j / kPairSlots) & 1u, s_abort,
                                                &g_das_tc_wait_error, 303)) {
                     tc_fence_after();
-                    const uint64_t wdesc =
-                        desc_sw128_kmajor(smem_u32(sW + (grp + kGroups * (j & 1)) * kWBytes));
-                    for (int kk = 0; kk < steps; ++kk) {
-                        int c = pos + kk;
-                        if (c >= C) c -= C;
-                        mma_f16(acc, wdesc + 2 * kk, desc_mn_chunk(ring + (uint32_t)(c * CB), NF),
-                                idesc, first ? 0u : 1u);
-                        first = false;
+                    // descriptors differ from the ring's first chunk and the
+                    // weight tile's first K-step only in their start-address
+                    // field (bits 0..13, shared address / 16), which the
+                    // offsets below never carry out of
+                    uint32_t wl = (j & 1) ? w_lo1 : w_lo0;
+                    uint32_t bl = b_lo0 + (uint32_t)pos * b_step;
+#pragma unroll
+                    for (int kk = 0; kk < kKW / kKC; ++kk) {
+                        if (kk < steps) {
+                            mma_f16(acc, ((uint64_t)w_hi << 32) | wl, ((uint64_t)b_hi << 32) | bl,
+                                    idesc, accf);
+                            accf = 1u;
+                            wl += 2;  // 32 bytes: the next 16 columns of the 128-byte rows
+                            bl += b_step;
+                            if (bl == b_end) bl = b_lo0;
+                        }
                     }
                     mma_commit(&gempty[j % kPairSlots]);
                 } else {
@@ -473,7 +489,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             __syncwarp();
         }
         if (lane == 0) {
-            s_used[grp] = first ? 0 : 1;
+            s_used[grp] = (int)accf;
             mma_commit(&done[grp]);  // arrives once this thread's MMAs have completed
         }
         __syncwarp();

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(192, 1)
                      const float* __restrict__ scale, float* __restrict__ out, int ldo) {
     using namespace mi;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_align1024(smem_raw);
     uint8_t* sW = base;                                  // [kStages] weight chunks
     uint8_t* sA = sW + kStages * kWBytes;                // [kTiles][kAChunks] activation chunks
     uint64_t* full = (uint64_t*)(sA + kTiles * kAChunks * kABytes);

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128, 1)
                     int skip_loads, unsigned long long wait_ns) {
     using namespace mg;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_align1024(smem_raw);
     uint8_t* sA = base;
     uint8_t* sB = base + kStages * kABytes;
     uint64_t* full = (uint64_t*)(sB + kStages * kBBytes);

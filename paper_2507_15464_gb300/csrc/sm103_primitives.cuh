@@ -13,6 +13,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// First 1024-byte-aligned byte of the dynamic shared memory.  The offset is
+// added to the shared-memory pointer itself (not computed through an integer
+// cast of it), so that pointers derived from the result stay in the shared
+// address space and their accesses compile to shared-memory instructions.
+__device__ __forceinline__ uint8_t* smem_align1024(uint8_t* smem_raw) {
+    return smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+}
+
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(gemm::Cfg<RESID>::kThreads, 1)
     using namespace gemm;
     using C = Cfg<RESID>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_align1024(smem_raw);
     uint8_t* sA = base + C::kOffA;  // [stage][part] BF16 tiles
     uint8_t* sB = base + C::kOffB;  // [buf][part][3] Toeplitz tiles
     uint8_t* sO = base + C::kOffO;  // [epilogue warp][2] output staging tiles
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(gemm2::kThreads, 1)
                         int kz, int taps, int adjoint, int nz, int nx, int nf) {
     using namespace gemm;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_align1024(smem_raw);
     uint8_t* sA = base + gemm2::kOffA;  // [stage] BF16 input chunks
     uint8_t* sB = base + gemm2::kOffB;  // [buf] band matrix G
     uint8_t* sO = base + gemm2::kOffO;  // [epilogue warp][2] output staging tiles
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
     using namespace gemm;
     using namespace vgem;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_align1024(smem_raw);
     uint8_t* sA = base + vgem::kOffA;
     uint8_t* sB = base + vgem::kOffB;
     uint8_t* sO = base + vgem::kOffO;
