@@ -340,11 +340,11 @@ def run_ours(args):
     # DRAM bytes of one das_tc_kernel launch (64 frames), from a one-pass ncu
     # capture of the current kernel (dram__bytes_read + dram__bytes_write);
     # None whenever the kernel changes after that capture
-    traffic = 693.8e6 if BATCH == 64 else None
+    traffic = 686.6e6 if BATCH == 64 else None
     # DRAM bytes of the step's two launches from the same capture: the repack
     # reads the batch and writes its staged copy, the DAS kernel reads that copy
     # (L2 serves the re-reads of neighbouring tiles) and writes the image
-    step_traffic = {"das_tc_pack_kernel": 1451.3e6, "das_tc_kernel": 693.8e6} \
+    step_traffic = {"das_tc_pack_kernel": 1450.9e6, "das_tc_kernel": 686.6e6} \
         if BATCH == 64 else None
     roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
             "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
@@ -355,12 +355,12 @@ def run_ours(args):
             "step_traffic": step_traffic,
             "step_traffic_over_algorithmic": (sum(step_traffic.values()) / alg_bytes
                                               if step_traffic else None),
-            "hw_counters": {"issue_active": 0.686, "tensor_pipe_active": 0.052,
-                            "warps_active": 0.373, "l2_hit_rate": 0.904,
-                            "warp_instructions_per_pair": 918,
+            "hw_counters": {"issue_active": 0.685, "tensor_pipe_active": 0.058,
+                            "warps_active": 0.373, "l2_hit_rate": 0.903,
+                            "warp_instructions_per_pair": 825,
                             "source": "ncu, profiles/das_tc_kernel_pw128_compound_64frames_f16.md"},
             "note": "instruction-issue- and latency-bound: 69 % of issue slots busy, "
-                    "mostly the weight-building warps; tensor pipe 5.2 % busy.  The frac above is "
+                    "mostly the weight-building warps; tensor pipe 5.8 % busy.  The frac above is "
                     "the algorithmic flops (10 per update) over a derived CUDA-core FP32 "
                     "peak; the hardware counters are the bound"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -426,28 +426,36 @@ def run_ours(args):
     # together); over at least 32 steps they weigh what they would in a
     # continuing stream at most 0.13 ms per step
     n_e2e = max(32, args.steps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # a plan freed by the garbage collector inside the loop would synchronise
     # the device (cudaFree) and drain the pipeline: collect first, then hold it
     import gc
-    gc.collect()
-    gc.disable()
-    e0.record(streamer.up)
-    for k in range(n_e2e):
-        streamer.submit(host_in[k & 1], host_out[k & 1])
-    streamer.down.wait_stream(streamer.comp)
-    e1.record(streamer.down)
-    torch.cuda.synchronize()
-    gc.enable()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    # The host -> device link is shared with the other GPUs of the machine, so
+    # a window of steps can run slower than the next; three windows, median
+    # reported, all listed
+    windows = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gc.collect()
+        gc.disable()
+        e0.record(streamer.up)
+        for k in range(n_e2e):
+            streamer.submit(host_in[k & 1], host_out[k & 1])
+        streamer.down.wait_stream(streamer.comp)
+        e1.record(streamer.down)
+        torch.cuda.synchronize()
+        gc.enable()
+        windows.append(e0.elapsed_time(e1) / n_e2e)
+    e2e_ms = sorted(windows)[1]
     ok_e2e = torch.equal(host_out[(n_e2e - 1) & 1], img.cpu())
     e2e_ms, serial_ms = max_over_ranks(torch, [e2e_ms, serial_ms], world, "cuda")
     first, count = P16.read_window()
     e2e = {"value": whole_job_mpix_s(BATCH, npx, world, e2e_ms), "unit": "Mpixels/s",
            "h2d_bytes_per_step": streamer.h2d_bytes, "d2h_bytes_per_step": img.numel() * 4,
            "ms_per_step": e2e_ms, "steps": n_e2e,
+           "windows_ms_per_step": windows,
            "form": "ops.DasStreamer: copies of neighbouring steps overlap the beamforming; "
-                   "the stream's first upload and last read-back are inside the timed region",
+                   "the stream's first upload and last read-back are inside each timed window; "
+                   "median of three windows",
            "upload": "the plan's read window of every record, samples %d..%d of %d "
                      "(das_upload_window; the samples DAS weights)"
                      % (first, first + count - 1, g["n_samples"]),
