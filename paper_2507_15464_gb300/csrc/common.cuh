@@ -68,6 +68,7 @@ struct Plan {
     // tensor-core DAS of FP16 plans: per-(tile, angle, element) sample windows
     int* tc_tab = nullptr;
     int2* tc_range = nullptr;
+    uint8_t* tc_rounds = nullptr;  // per tile: its rounds of one or two pairs
     int tc_tiles_x = 0, tc_tiles = 0;
     bool tc_ok = false;     // every window fits the 64-sample operand tile
     int tc_mode = 1;        // 0: CUDA cores only, 1: tensor cores for >= 16 FP16 frames

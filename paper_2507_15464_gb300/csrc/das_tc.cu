@@ -30,9 +30,10 @@
 //    fit one 64-column weight tile together (at plan creation, greedily from
 //    the first pair), and the groups take alternate rounds.  Every thread
 //    owns one pixel (one row of W_an, one tensor-memory lane): it erases the
-//    16-byte chunks it wrote two rounds ago and writes each pair's four
-//    weights as swizzled chunks of a 128-byte-swizzled K-major weight tile
-//    (two per group), the second pair's columns after the first's.
+//    8-byte words it wrote two rounds ago and writes each pair's four weights
+//    as the one or two 8-byte words they cover in its row of a 128-byte-
+//    swizzled K-major weight tile (two per group), the second pair's columns
+//    after the first's.
 //  - warps 10, 11: the MMA warps of group 0 / group 1.  Builders and MMA warp
 //    meet at a named barrier once per round; then the MMA warp issues the
 //    round's K-steps into the group's own accumulator while the builders write
@@ -76,11 +77,14 @@ constexpr int kGroups = 2;                // builder groups, one accumulator eac
 constexpr int kWTiles = 2 * kGroups;      // weight tiles: two per group
 constexpr int kWBytes = kM * kKW * 2;     // 16 KB
 constexpr int kPairSlots = 8;             // rounds of a group in flight (barrier slots)
-// Window entry, 16 bits: 2 * k0 + (8 if the pair is the second of its round)
-// + K-steps (0..4); k0 is a multiple of 8 in [-kMaxK0, kMaxK0].
+// Window entry, 16 bits: 2 * k0 + K-steps (0..4); k0 is a multiple of 8 in
+// [-kMaxK0, kMaxK0].
 constexpr int kMaxK0 = 16376;
-constexpr int kSecond = 8;
 __host__ __device__ constexpr int entry_k0(int e) { return (e >> 4) * 8; }
+// Round descriptor, 8 bits: the round's K-steps (0..4) + kTwoPairs if it
+// holds two pairs.
+constexpr int kTwoPairs = 8;
+__host__ __device__ constexpr int round_pairs(int rd) { return 1 + (rd >> 3); }
 constexpr int kMinChunks = 6, kMaxChunks = 32;  // chunks per group ring
 // per group: one producer warp, four builder warps, one MMA warp
 constexpr int kBuilderWarp0 = kGroups;            // warps [0, kGroups): producers
@@ -93,11 +97,13 @@ constexpr size_t kSmemTwoPerSM = 115712;  // (228 KB - 2 x 1 KB reserved) / 2
 constexpr size_t kSmemMax = 227 * 1024;
 // one K-step chunk = 16 sample rows of NF frames
 __host__ __device__ constexpr int chunk_bytes(int NF) { return kKC * NF * 2; }
-// align | weight tiles | chunk rings | barriers, flags (1 KB) |
-// transmit split [A][kM] int2 | window entries [A * NE] int16
+// align | weight tiles | chunk rings | barriers, flags (512 B) |
+// transmit split [A][kM] int2 | window entries [A * NE] int16 |
+// round descriptors [A * NE] uint8 (a tile has at most one round per pair)
+constexpr size_t kFlagBytes = 512;
 __host__ __device__ constexpr size_t fixed_bytes(int A, int NE) {
-    return 1024 + (size_t)kWTiles * kWBytes + 1024 + (size_t)A * kM * 8 +
-           (((size_t)A * NE * 2 + 15) & ~(size_t)15);
+    return 1024 + (size_t)kWTiles * kWBytes + kFlagBytes + (size_t)A * kM * 8 +
+           (((size_t)A * NE * 2 + 15) & ~(size_t)15) + (((size_t)A * NE + 15) & ~(size_t)15);
 }
 __host__ __device__ constexpr size_t smem_bytes(int NF, int C, int A, int NE) {
     return fixed_bytes(A, NE) + (size_t)kGroups * C * chunk_bytes(NF);
@@ -180,18 +186,10 @@ __device__ __forceinline__ uint64_t desc_mn_chunk(uint32_t smem_addr, int NF) {
            ((uint64_t)1 << 46) | (layout << 61);
 }
 
-// Place the 4 FP16 weights `v` (packed in 64 bits) at half offset o (0..7)
-// of a 32-byte span: lo / hi are the two 16-byte chunks.
-__device__ __forceinline__ void place4(uint64_t v, int o, uint4& lo, uint4& hi) {
-    const int s = (o & 3) * 16;
-    const uint64_t a = v << s, b = s ? v >> (64 - s) : 0ull;
-    if (o < 4) {
-        lo = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
-        hi = make_uint4(0, 0, 0, 0);
-    } else {
-        lo = make_uint4(0, 0, (uint32_t)a, (uint32_t)(a >> 32));
-        hi = make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0, 0);
-    }
+// 8-byte word w (0..15) of a weight-tile row: 16-byte chunk w / 2, XORed
+// with the row's swizzle, half w % 2.
+__device__ __forceinline__ uint64_t* row_word(uint8_t* row, int w, int swz) {
+    return reinterpret_cast<uint64_t*>(row + ((((w >> 1) ^ swz) << 4) | ((w & 1) << 3)));
 }
 
 // Hand-off between group g's 128 builders and its MMA warp (160 threads):
@@ -215,18 +213,13 @@ __device__ __forceinline__ float builder_apod(float dxs, float zs, float fnum) {
     return cw * cw;
 }
 
-// Pairs in the round that starts at pair q: two when pair q + 1 is marked as
-// the second of its round.
-__device__ __forceinline__ int round_len(const int16_t* s_tab, int q, int npairs) {
-    return (q + 1 < npairs && (s_tab[q + 1] & dtc::kSecond)) ? 2 : 1;
-}
-
-// First pair of group grp's next round after the one at q (rounds alternate
-// between the groups); npairs or more when there is none.
-__device__ __forceinline__ int next_round(const int16_t* s_tab, int q, int npairs) {
-    int q2 = q + round_len(s_tab, q, npairs);
-    if (q2 < npairs) q2 += round_len(s_tab, q2, npairs);
-    return q2;
+// First pair of a group's next round, after its round r of `len` pairs that
+// starts at pair q: the other group's round r + 1 comes in between (rounds
+// alternate between the groups).  npairs or more when there is none.
+__device__ __forceinline__ int next_round(const uint8_t* s_rd, int r, int q, int len,
+                                          int npairs) {
+    const int q1 = q + len;
+    return q1 < npairs ? q1 + dtc::round_pairs(s_rd[r + 1]) : q1;
 }
 
 // Per-(tile, angle, element) window: entry = 2 k0 + ksteps, k0 a multiple of
@@ -283,8 +276,8 @@ __global__ void das_tc_table_kernel(DasDev d, int tiles_x, int tiles, int* __res
 template <int INTERP>
 __global__ void __launch_bounds__(dtc::kThreads, 2)
     das_tc_kernel(const __half* __restrict__ packed, DasDev d, const int* __restrict__ tab,
-                  const int2* __restrict__ range, int tiles_x, int nf, int NF, int C,
-                  float* __restrict__ img) {
+                  const int2* __restrict__ range, const uint8_t* __restrict__ rounds,
+                  int tiles_x, int nf, int NF, int C, float* __restrict__ img) {
     using namespace dtc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = smem_align1024(smem_raw);
@@ -301,8 +294,9 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     uint32_t* tmem_slot = (uint32_t*)(done + kGroups);
     volatile int* s_abort = (volatile int*)(tmem_slot + 1);
     int* s_used = (int*)(tmem_slot + 2);                       // [kGroups]
-    int2* s_base = (int2*)((uint8_t*)full + 1024);             // [A][kM]: transmit split
+    int2* s_base = (int2*)((uint8_t*)full + kFlagBytes);       // [A][kM]: transmit split
     int16_t* s_tab = (int16_t*)(s_base + A * kM);              // [pair]: window entries
+    uint8_t* s_rd = (uint8_t*)s_tab + (((size_t)A * NE * 2 + 15) & ~(size_t)15);  // [round]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // deepest tiles first: their apertures span the most elements, so the
@@ -328,7 +322,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         *s_abort = 0;
         fence_barrier_init();
     }
-    // zero the weight tiles once; afterwards only written chunks are erased
+    // zero the weight tiles once; afterwards only written words are erased
     for (int i = threadIdx.x; i < kWTiles * kWBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(sW)[i] = make_uint4(0, 0, 0, 0);
     // this tile's window entries (pair order: element-major, angle-minor) and
@@ -336,8 +330,11 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
     // per pair
     {
         const int* tt = tab + (size_t)tile * A * NE;
-        for (int i = threadIdx.x; i < npairs; i += blockDim.x)
+        const uint8_t* tr = rounds + (size_t)tile * A * NE;
+        for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
             s_tab[i] = (int16_t)__ldg(tt + (i % A) * NE + n_lo + i / A);
+            s_rd[i] = __ldg(tr + i);
+        }
         for (int i = threadIdx.x; i < A * kM; i += blockDim.x) {
             const int a = i / kM, m = i % kM;
             const int ix = tx * kTX + m % kTX, iz = tz * kTZ + m / kTX;
@@ -369,11 +366,14 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             int qa = 0, n = n_lo, a = 0;  // pair qa is (element n, angle a)
             uint32_t pend = 0;            // K-steps of the rounds in flight, 3 bits per slot
             bool bad = false;
-            int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
-            for (; q < npairs && !bad; q = next_round(s_tab, q, npairs), ++j) {
-                const int len = round_len(s_tab, q, npairs);
+            // global round r = 2 j + grp starts at pair q
+            int q = grp == 0 || npairs == 0 ? 0 : round_pairs(s_rd[0]);
+            for (int len; q < npairs && !bad;
+                 q = next_round(s_rd, 2 * j + grp, q, len, npairs), ++j) {
+                const int rd = s_rd[2 * j + grp];
+                len = round_pairs(rd);
+                const int steps = rd & 7;
                 const int e0 = s_tab[q], e1 = len == 2 ? s_tab[q + 1] : 0;
-                const int steps = (e0 & 7) + (e1 & 7);
                 // reuse of the round slot, and room for this round's chunks:
                 // retire the oldest rounds in flight
                 while (!bad && oldest < j && (oldest <= j - kPairSlots || free_chunks < steps)) {
@@ -444,8 +444,10 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         const uint32_t w_lo0 = (uint32_t)w0, w_hi = (uint32_t)(w0 >> 32);
         const uint32_t w_lo1 =
             (uint32_t)desc_sw128_kmajor(smem_u32(sW + (grp + kGroups) * kWBytes));
-        int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
-        for (; q < npairs; q = next_round(s_tab, q, npairs), ++j) {
+        int q = grp == 0 || npairs == 0 ? 0 : round_pairs(s_rd[0]);
+        for (int len; q < npairs; q = next_round(s_rd, 2 * j + grp, q, len, npairs), ++j) {
+            const int rd = s_rd[2 * j + grp];
+            len = round_pairs(rd);
             // Round j - 1's MMAs must be complete before this barrier: past it the
             // builders write round j + 1 into the tile round j - 1 read.  (Its MMAs
             // ran while the builders wrote round j, so this rarely waits.)
@@ -455,8 +457,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                                           &g_das_tc_wait_error, 304);
             // the group's weight tile of round j is written (leave together on an abort)
             if (group_bar(grp, bad || *s_abort)) break;
-            const int steps =
-                (s_tab[q] & 7) + (round_len(s_tab, q, npairs) == 2 ? s_tab[q + 1] & 7 : 0);
+            const int steps = rd & 7;
             if (lane == 0) {
                 if (!bad && mbar_wait_or_abort(&gfull[j % kPairSlots],
                                                (uint32_t)(j / kPairSlots) & 1u, s_abort,
@@ -534,25 +535,21 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             if (n + 1 <= n_hi) dxs_next = __ldg(d.dxs + (size_t)(n + 1) * d.nx + ixc);
         }
         int j = 0;
-        int q = grp == 0 || npairs == 0 ? 0 : round_len(s_tab, 0, npairs);
+        int q = grp == 0 || npairs == 0 ? 0 : round_pairs(s_rd[0]);
         a = q;
         for (; q < npairs; ++j) {
-            const int len = round_len(s_tab, q, npairs);
+            const int len = round_pairs(s_rd[2 * j + grp]);
             // the tile was last read by this group's round j - 2, whose MMAs the
             // MMA warp saw complete before the previous group barrier
             {
                 uint8_t* W = rowp + (grp + kGroups * (j & 1)) * kWBytes;
                 if (r0 >= 0) {
-                    *reinterpret_cast<uint4*>(W + (((r0 >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
-                    if ((r0 & 7) > 4)
-                        *reinterpret_cast<uint4*>(W + ((((r0 >> 3) + 1) ^ swz) << 4)) =
-                            make_uint4(0, 0, 0, 0);
+                    *row_word(W, r0 >> 2, swz) = 0ull;
+                    if (r0 & 3) *row_word(W, (r0 >> 2) + 1, swz) = 0ull;
                 }
                 if (r1 >= 0) {
-                    *reinterpret_cast<uint4*>(W + (((r1 >> 3) ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
-                    if ((r1 & 7) > 4)
-                        *reinterpret_cast<uint4*>(W + ((((r1 >> 3) + 1) ^ swz) << 4)) =
-                            make_uint4(0, 0, 0, 0);
+                    *row_word(W, r1 >> 2, swz) = 0ull;
+                    if (r1 & 3) *row_word(W, (r1 >> 2) + 1, swz) = 0ull;
                 }
                 r0 = -1;
                 r1 = -1;
@@ -606,12 +603,12 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                             const uint64_t pk =
                                 (uint64_t)*reinterpret_cast<const uint32_t*>(&h01) |
                                 ((uint64_t)*reinterpret_cast<const uint32_t*>(&h23) << 32);
+                            // the taps' 8 bytes at half offset c of the row: one
+                            // word, or the two words they straddle
                             c += col0;
-                            uint4 lo, hi;
-                            place4(pk, c & 7, lo, hi);
-                            *reinterpret_cast<uint4*>(W + (((c >> 3) ^ swz) << 4)) = lo;
-                            if ((c & 7) > 4)
-                                *reinterpret_cast<uint4*>(W + ((((c >> 3) + 1) ^ swz) << 4)) = hi;
+                            const int sh = (c & 3) * 16;
+                            *row_word(W, c >> 2, swz) = pk << sh;
+                            if (sh) *row_word(W, (c >> 2) + 1, swz) = pk >> (64 - sh);
                             if (p)
                                 r1 = c;
                             else
@@ -630,7 +627,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             fence_proxy_async_smem();
             if (group_bar(grp, *s_abort)) break;
             // (n, a) of the first pair of the group's next round
-            const int q2 = next_round(s_tab, q, npairs);
+            const int q2 = next_round(s_rd, 2 * j + grp, q, len, npairs);
             a += q2 - (q + len - 1);
             q = q2;
         }
@@ -675,36 +672,32 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
 }
 
 // Cut each tile's pairs (element-major, angle-minor, from its first
-// contributing element) into rounds, greedily from the first pair: a pair
-// joins the round of the pair before it when that round holds one pair and
-// their K-steps fit one weight tile.  The second pair of a round is marked in
-// its entry.  One thread per tile.
-__global__ void das_tc_round_kernel(int A, int NE, int tiles, int* __restrict__ tab,
-                                    const int2* __restrict__ range) {
+// contributing element) into rounds of one or two consecutive pairs,
+// greedily from the first pair: a pair joins the round of the pair before it
+// when that round holds one pair and their K-steps fit one weight tile.
+// Round r of the tile is described by rounds[tile][r] (kTwoPairs + K-steps);
+// a tile has at most one round per pair.  One thread per tile.
+__global__ void das_tc_round_kernel(int A, int NE, int tiles, const int* __restrict__ tab,
+                                    const int2* __restrict__ range,
+                                    uint8_t* __restrict__ rounds) {
     const int tile = blockIdx.x * blockDim.x + threadIdx.x;
     if (tile >= tiles) return;
     const int2 rg = range[tile];
     if (rg.y < rg.x) return;
     const int npairs = (rg.y - rg.x + 1) * A;
-    int* tt = tab + (size_t)tile * A * NE + rg.x;
-    int q = 0, n = 0, a = 0;  // pair q is (element rg.x + n, angle a)
-    int e = tt[0];
-    while (q < npairs) {
-        const int q1 = q + 1, a1 = a + 1 < A ? a + 1 : 0, n1 = a + 1 < A ? n : n + 1;
-        if (q1 >= npairs) break;
-        const int e1 = tt[a1 * NE + n1];
-        if ((e & 7) + (e1 & 7) <= dtc::kMaxSteps) {
-            tt[a1 * NE + n1] = e1 | dtc::kSecond;
-            // the round is full: the next one starts at pair q + 2
-            q = q1 + 1;
-            a = a1 + 1 < A ? a1 + 1 : 0;
-            n = a1 + 1 < A ? n1 : n1 + 1;
-            if (q < npairs) e = tt[a * NE + n];
+    const int* tt = tab + (size_t)tile * A * NE + rg.x;
+    uint8_t* out = rounds + (size_t)tile * A * NE;
+    int r = 0;
+    for (int q = 0; q < npairs;) {
+        // pair q is (element rg.x + q / A, angle q % A)
+        const int s0 = tt[(q % A) * NE + q / A] & 7;
+        const int s1 = q + 1 < npairs ? tt[((q + 1) % A) * NE + (q + 1) / A] & 7 : dtc::kMaxSteps + 1;
+        if (s0 + s1 <= dtc::kMaxSteps) {
+            out[r++] = (uint8_t)(dtc::kTwoPairs + s0 + s1);
+            q += 2;
         } else {
-            q = q1;
-            a = a1;
-            n = n1;
-            e = e1;
+            out[r++] = (uint8_t)s0;
+            q += 1;
         }
     }
 }
@@ -733,10 +726,16 @@ int das_tc_prepare(Plan& P) {
     const size_t ntab = (size_t)P.tc_tiles * d.n_angles * d.n_elem;
     P.tc_ok = false;
     void* buf = nullptr;
-    TIDAS_CUDA(cudaMalloc(&buf, ntab * 4 + (size_t)P.tc_tiles * 8 + 512));
+    // window entries | per-tile element range | round descriptors | flag
+    const size_t off_range = (ntab * 4 + 255) & ~(size_t)255;
+    const size_t off_rounds = (off_range + (size_t)P.tc_tiles * 8 + 255) & ~(size_t)255;
+    const size_t off_bad = (off_rounds + ntab + 255) & ~(size_t)255;
+    TIDAS_CUDA(cudaMalloc(&buf, off_bad + 256));
     P.tc_tab = (int*)buf;
-    P.tc_range = (int2*)((char*)buf + ((ntab * 4 + 255) & ~(size_t)255));
-    int* d_bad = (int*)((char*)P.tc_range + P.tc_tiles * 8);
+    P.tc_range = (int2*)((char*)buf + off_range);
+    P.tc_rounds = (uint8_t*)buf + off_rounds;
+    int* d_bad = (int*)((char*)buf + off_bad);
+    TIDAS_CUDA(cudaMemset(P.tc_rounds, 0, ntab));
     std::vector<int2> init(P.tc_tiles, make_int2(INT_MAX, INT_MIN));
     TIDAS_CUDA(cudaMemcpy(P.tc_range, init.data(), P.tc_tiles * 8, cudaMemcpyHostToDevice));
     TIDAS_CUDA(cudaMemset(d_bad, 0, 4));
@@ -746,7 +745,7 @@ int das_tc_prepare(Plan& P) {
     int rc = check_launch("das_tc_table_kernel");
     if (rc) return rc;
     das_tc_round_kernel<<<(P.tc_tiles + 127) / 128, 128>>>(d.n_angles, d.n_elem, P.tc_tiles,
-                                                          P.tc_tab, P.tc_range);
+                                                          P.tc_tab, P.tc_range, P.tc_rounds);
     rc = check_launch("das_tc_round_kernel");
     if (rc) return rc;
     int bad = 0;
@@ -790,12 +789,12 @@ int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_
         TIDAS_CUDA(cudaFuncSetAttribute(das_tc_kernel<TIDAS_INTERP_CUBIC>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         das_tc_kernel<TIDAS_INTERP_CUBIC><<<grid, kThreads, smem, st>>>(
-            packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF, C, img);
+            packed, d, P.tc_tab, P.tc_range, P.tc_rounds, P.tc_tiles_x, nf, NF, C, img);
     } else {
         TIDAS_CUDA(cudaFuncSetAttribute(das_tc_kernel<TIDAS_INTERP_LINEAR>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         das_tc_kernel<TIDAS_INTERP_LINEAR><<<grid, kThreads, smem, st>>>(
-            packed, d, P.tc_tab, P.tc_range, P.tc_tiles_x, nf, NF, C, img);
+            packed, d, P.tc_tab, P.tc_range, P.tc_rounds, P.tc_tiles_x, nf, NF, C, img);
     }
     return check_launch("das_tc_kernel");
 }
