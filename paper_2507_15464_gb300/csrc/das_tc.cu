@@ -186,10 +186,11 @@ __device__ __forceinline__ uint64_t desc_mn_chunk(uint32_t smem_addr, int NF) {
            ((uint64_t)1 << 46) | (layout << 61);
 }
 
-// 8-byte word w (0..15) of a weight-tile row: 16-byte chunk w / 2, XORed
-// with the row's swizzle, half w % 2.
-__device__ __forceinline__ uint64_t* row_word(uint8_t* row, int w, int swz) {
-    return reinterpret_cast<uint64_t*>(row + ((((w >> 1) ^ swz) << 4) | ((w & 1) << 3)));
+// The 8-byte word of a weight-tile row that holds column c (0..63): byte
+// 2 c rounded down to 8, with the 16-byte chunk index (bits 4..6) XORed with
+// the row's swizzle; swz16 = swizzle << 4.
+__device__ __forceinline__ uint64_t* row_word(uint8_t* row, int c, int swz16) {
+    return reinterpret_cast<uint64_t*>(row + (((c << 1) & 0x78) ^ swz16));
 }
 
 // Hand-off between group g's 128 builders and its MMA warp (160 threads):
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         const int ixc = valid ? ix : 0, izc = valid ? iz : 0;
         const float zs = __ldg(d.zs + izc);
         uint8_t* const rowp = sW + (m >> 3) * 1024 + (m & 7) * 128;
-        const int swz = m & 7;
+        const int swz16 = (m & 7) << 4;
         float exc = 0.f;
         // apodized interpolation weights of element n as polynomials in the
         // fraction phi, with the Hann weight w folded into the coefficients
@@ -544,12 +545,12 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
             {
                 uint8_t* W = rowp + (grp + kGroups * (j & 1)) * kWBytes;
                 if (r0 >= 0) {
-                    *row_word(W, r0 >> 2, swz) = 0ull;
-                    if (r0 & 3) *row_word(W, (r0 >> 2) + 1, swz) = 0ull;
+                    *row_word(W, r0, swz16) = 0ull;
+                    if (r0 & 3) *row_word(W, r0 + 4, swz16) = 0ull;
                 }
                 if (r1 >= 0) {
-                    *row_word(W, r1 >> 2, swz) = 0ull;
-                    if (r1 & 3) *row_word(W, (r1 >> 2) + 1, swz) = 0ull;
+                    *row_word(W, r1, swz16) = 0ull;
+                    if (r1 & 3) *row_word(W, r1 + 4, swz16) = 0ull;
                 }
                 r0 = -1;
                 r1 = -1;
@@ -607,8 +608,8 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                             // word, or the two words they straddle
                             c += col0;
                             const int sh = (c & 3) * 16;
-                            *row_word(W, c >> 2, swz) = pk << sh;
-                            if (sh) *row_word(W, (c >> 2) + 1, swz) = pk >> (64 - sh);
+                            *row_word(W, c, swz16) = pk << sh;
+                            if (sh) *row_word(W, c + 4, swz16) = pk >> (64 - sh);
                             if (p)
                                 r1 = c;
                             else
