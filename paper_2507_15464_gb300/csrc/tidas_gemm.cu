@@ -332,6 +332,28 @@ __global__ void __launch_bounds__(gemm::Cfg<RESID>::kThreads, 1)
                         v[i] = __ldcs(reinterpret_cast<const float4*>(
                             in32 + ((size_t)f * nz + I.z) * nx + x));
                 }
+                // L2 prefetch of the next chunk (of this item, else the next
+                // item's first): row ct of it, its two 128-byte lines
+                {
+                    int pz = I.z, pm = I.m0, pc = c + 1;
+                    bool more = pc <= 2 * I.s1;
+                    if (!more && it + 1 < it_end) {
+                        const Item J = decode(it + 1, nh, nm, ntiles);
+                        pz = J.z;
+                        pm = J.m0;
+                        pc = 2 * J.s0;
+                        more = true;
+                    }
+                    const int f = pm + ct;
+                    if (more && f < nf) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int x = kKC * pc - 32 + 32 * h;
+                            if (x >= 0 && x < nx)
+                                prefetch_l2(in32 + ((size_t)f * nz + pz) * nx + x);
+                        }
+                    }
+                }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int id = ct + 128 * i;
