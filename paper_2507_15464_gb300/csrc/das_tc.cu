@@ -193,6 +193,24 @@ __device__ __forceinline__ uint64_t* row_word(uint8_t* row, int c, int swz16) {
     return reinterpret_cast<uint64_t*>(row + (((c << 1) & 0x78) ^ swz16));
 }
 
+// Two single-precision FMAs / products in one packed instruction (sm_100
+// f32x2): each half is rounded exactly as the scalar fmaf / multiply.
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Hand-off between group g's 128 builders and its MMA warp (160 threads):
 // a barrier that both sides wait on, once per round, which also tells every
 // participant whether any of them has given up.  While the builders write
@@ -512,15 +530,20 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
         // fraction phi, with the Hann weight w folded into the coefficients
         // (Horner form): cubic Keys, w w0 = phi (phi (ca phi + cw) + ca),
         // w w1 = phi^2 (cc phi + cd) + cw, w w2 = phi (phi (cf - cc phi) + ch),
-        // w w3 = phi^2 (ch phi - ch); linear w (1 - phi), w phi
-        float cw = 0.f, ca = 0.f, cc = 0.f, cd = 0.f, cf = 0.f, ch = 0.f;
+        // w w3 = phi^2 (ch phi - ch); linear w (1 - phi), w phi.  The cubic
+        // coefficients are kept as the pairs that evaluate (w0, w2) and the
+        // inner terms of (w1, w3) in packed instructions.
+        float cw = 0.f;
+        uint64_t k02a = 0, k02b = 0, k02c = 0, k13a = 0, k13b = 0;
         auto set_weight = [&](float w) {
+            const float ca = -0.5f * w, cc = 1.5f * w, cd = -2.5f * w, cf = 2.f * w,
+                        ch = 0.5f * w;
             cw = w;
-            ca = -0.5f * w;
-            cc = 1.5f * w;
-            cd = -2.5f * w;
-            cf = 2.f * w;
-            ch = 0.5f * w;
+            k02a = f2(ca, -cc);
+            k02b = f2(w, cf);
+            k02c = f2(ca, ch);
+            k13a = f2(cc, ch);
+            k13b = f2(cd, -ch);
         };
         // the column of the first tap this thread wrote into each of the
         // group's two tiles, per pair of the round that wrote it (-1: none):
@@ -584,10 +607,13 @@ __global__ void __launch_bounds__(dtc::kThreads, 2)
                         int c;
                         if (INTERP == TIDAS_INTERP_CUBIC) {
                             const float p2 = phi * phi;
-                            v0 = fmaf(fmaf(ca, phi, cw), phi, ca) * phi;
-                            v1 = fmaf(fmaf(cc, phi, cd), p2, cw);
-                            v2 = fmaf(fmaf(-cc, phi, cf), phi, ch) * phi;
-                            v3 = fmaf(ch, phi, -ch) * p2;
+                            const uint64_t P = f2(phi, phi);
+                            const uint64_t t02 = f2_mul(f2_fma(f2_fma(k02a, P, k02b), P, k02c), P);
+                            const uint64_t t13 = f2_fma(k13a, P, k13b);
+                            v0 = f2_lo(t02);
+                            v2 = f2_hi(t02);
+                            v1 = fmaf(f2_lo(t13), p2, cw);
+                            v3 = f2_hi(t13) * p2;
                             c = i - 1 - k0;
                         } else {
                             v0 = fmaf(-cw, phi, cw);
