@@ -51,6 +51,7 @@ struct DasDev {
     float elem0_s;       // x_0 * fs / c
     float pitch_s;       // pitch * fs / c
     const float* ptab;   // [3][2 kJ + 1]: exp(-beta j^2), cos(pi wcar j), sin(pi wcar j)
+    const float2* carr;  // carr[k] = e^{i pi wcar k}, valid for k = -kJ .. n_samples + kJ - 1
 };
 
 // Host-side plan object.
@@ -94,6 +95,24 @@ __device__ __forceinline__ float apod_weight(float dxs, float zs, float fnum) {
     if (fabsf(r) > 0.5f) return 0.f;
     float cw = cospif(r);
     return cw * cw;
+}
+
+// Two single-precision FMAs / products in one packed instruction (sm_100
+// f32x2): each half is rounded exactly as the scalar fmaf / multiply.
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
 // Keys (a = -0.5) weights of samples i-1, i, i+1, i+2 at fraction phi.

@@ -605,10 +605,17 @@ __global__ void __launch_bounds__(256) synth_grid_kernel(DasDev d, const float* 
 // pixels whose pulse reaches them.  The delay grows with depth down a
 // column (d/dz of x sin + z cos + |r - x_n| is cos + z / |r - x_n| > 0), so
 // those pixels are a contiguous run found by binary search over the
-// column's integer delays.  Per (pixel, thread) the pulse is evaluated
-// exactly at the thread's first sample and carried over its kGS samples by
-// recurrences (envelope ratio exp(-beta (2 t + 1)), carrier rotation).  No
-// atomics; each sample is summed in a fixed order (columns, then depth).
+// column's integer delays.  The pulse is the real part of
+// env(t) e^{i pi wcar t} (a1), so
+//     rf[k] = Re( e^{i pi wcar k} G[k] ),  G[k] = sum_p c_p env(k - u_p),
+// with the complex amplitude c_p = v_p e^{-i pi wcar u_p} formed once per
+// pixel and row (e^{-i pi wcar i} from the plan's integer-sample carrier
+// table, the fraction's phase by sincospi of a small argument).  At the
+// thread's samples k0 + q the envelope factors as
+//     env(t0 + q) = exp(-beta t0^2) R^q exp(-beta q^2),  R = exp(-2 beta t0),
+// t0 = k0 - u_p, and the last factor, the same for every pixel, is applied
+// once per sample after the sum.  No atomics; each sample is summed in a
+// fixed order (columns, then depth).
 constexpr int kGS = 16;
 __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
                                                                 const float* __restrict__ reflT,
@@ -617,20 +624,17 @@ __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
     const int NZ = d.nz, NX = d.nx, S = d.n_samples;
     int* ui = reinterpret_cast<int*>(sm);  // [NZ] integer delay of the column's pixels
     float* uf = sm + NZ;                   // [NZ] fraction
-    float* vz = uf + NZ;                   // [NZ] reflectivity of the column
+    float* cre = uf + NZ;                  // [NZ] complex amplitude v e^{-i pi wcar u}
+    float* cim = cre + NZ;
     const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
     const float* rt = reflT + (size_t)f * NX * NZ;
     const int hi_tap = (int)ceilf(d.thalf) + 1;
-    // constant recurrence factors: exp(-2 beta) and the carrier's rotation by one sample
-    const float h = expf(-2.f * d.beta);
-    float sw, cw;
-    sincospif(d.wcar, &sw, &cw);
     float* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
     for (int base = 0; base < S; base += kGS * (int)blockDim.x) {
         const int k0 = base + kGS * (int)threadIdx.x;
-        float acc[kGS];
+        float gr[kGS], gi[kGS];  // G[k0 + q] / exp(-beta q^2)
 #pragma unroll
-        for (int q = 0; q < kGS; ++q) acc[q] = 0.f;
+        for (int q = 0; q < kGS; ++q) gr[q] = gi[q] = 0.f;
         for (int ix = 0; ix < NX; ++ix) {
             __syncthreads();
             const float dxs = __ldg(d.dxs + (size_t)n * NX + ix);
@@ -640,7 +644,19 @@ __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
                 pixel_delay(d, a, ix, iz, rx_excess(dxs, __ldg(d.zs + iz)), i, phi);
                 ui[iz] = i;
                 uf[iz] = phi;
-                vz[iz] = __ldg(rt + (size_t)ix * NZ + iz);
+                float v = __ldg(rt + (size_t)ix * NZ + iz);
+                // a pixel whose support misses the record adds nothing
+                if (i < -hi_tap || i >= S + hi_tap) v = 0.f;
+                float zr = 0.f, zi = 0.f;
+                if (v != 0.f) {
+                    const float2 ci = __ldg(d.carr + i);
+                    float sp, cp;
+                    sincospif(d.wcar * phi, &sp, &cp);
+                    zr = v * (ci.x * cp - ci.y * sp);
+                    zi = -v * (ci.x * sp + ci.y * cp);
+                }
+                cre[iz] = zr;
+                cim[iz] = zi;
             }
             __syncthreads();
             if (k0 >= S) continue;
@@ -658,33 +674,35 @@ __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
                 if (ui[mid] <= want_hi) lo2 = mid + 1; else hi2 = mid;
             }
             for (int iz = lo; iz < lo2; ++iz) {
-                const float v = vz[iz];
-                if (v == 0.f) continue;
+                const float zr = cre[iz], zi = cim[iz];
+                if (zr == 0.f && zi == 0.f) continue;
                 const int i = ui[iz];
                 const float phi = uf[iz];
-                const int jlo = (int)ceilf(phi - d.thalf), jhi = (int)floorf(phi + d.thalf);
-                const int j0 = k0 - i;  // tap index of this thread's first sample
+                // this thread's samples k0 + q inside the support: tap j = k0 + q - i
+                const int j0 = k0 - i;
+                const int qlo = (int)ceilf(phi - d.thalf) - j0, qhi = (int)floorf(phi + d.thalf) - j0;
                 const float t0 = (float)j0 - phi;
-                float e = v * expf(-d.beta * t0 * t0);
-                float r = expf(-d.beta * (2.f * t0 + 1.f));
-                float sn, cs;
-                sincospif(d.wcar * t0, &sn, &cs);
+                const float e0 = expf(-d.beta * t0 * t0);
+                const float R = expf(-2.f * d.beta * t0);
+                const float er = e0 * zr, ei = e0 * zi;
+                float pw = 1.f;  // R^q
 #pragma unroll
                 for (int q = 0; q < kGS; ++q) {
-                    const int j = j0 + q;
-                    if (j >= jlo && j <= jhi) acc[q] = fmaf(e, cs, acc[q]);
-                    e *= r;
-                    r *= h;
-                    const float c2 = cs * cw - sn * sw;
-                    sn = fmaf(sn, cw, cs * sw);
-                    cs = c2;
+                    if (q >= qlo && q <= qhi) {
+                        gr[q] = fmaf(pw, er, gr[q]);
+                        gi[q] = fmaf(pw, ei, gi[q]);
+                    }
+                    pw *= R;
                 }
             }
         }
         if (k0 < S) {
 #pragma unroll
             for (int q = 0; q < kGS; ++q)
-                if (k0 + q < S) out[k0 + q] = acc[q];
+                if (k0 + q < S) {
+                    const float2 ck = __ldg(d.carr + k0 + q);
+                    out[k0 + q] = expf(-d.beta * (float)(q * q)) * (gr[q] * ck.x - gi[q] * ck.y);
+                }
         }
     }
 }
@@ -710,7 +728,7 @@ __global__ void transpose_grid_kernel(const float* __restrict__ in, float* __res
 
 int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, cudaStream_t st) {
     const DasDev& d = P.dev;
-    const size_t smem_g = (size_t)3 * d.nz * sizeof(float);
+    const size_t smem_g = (size_t)4 * d.nz * sizeof(float);
     if (smem_g <= 200 * 1024) {
         float* reflT = nullptr;
         TIDAS_CUDA(cudaMallocAsync((void**)&reflT, sizeof(float) * (size_t)nf * d.nz * d.nx, st));
@@ -738,19 +756,37 @@ int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, 
 }
 
 // ------------------------------------------------ synthesis transpose
-// One thread per pixel: correlate every channel row with the pulse delayed
-// to the pixel's round-trip time.  Same taps as synth_grid_kernel.
-__global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const float* __restrict__ rf,
+// The pulse is the real part of env(t) e^{i pi wcar t} (a1): with the channel
+// rows rotated to rfc[k] = rf[k] e^{i pi wcar k}, the correlation of row
+// (a, n) with the pulse delayed to u = i + phi is
+//     sum_m rf[m] p(m - u) = Re( e^{-i pi wcar (i + phi)} sum_j rfc[i + j] env(j - phi) ),
+// j over the truncated support.  env(j - phi) follows the recurrence
+// env(t + 1) = env(t) r(t), r(t) = exp(-beta (2 t + 1)), r(t + 1) = r(t) exp(-2 beta).
+// rfc[k] = rf[k] carr[k], one thread per sample.
+__global__ void synth_rotate_kernel(DasDev d, const float* __restrict__ rf, float2* __restrict__ rfc,
+                                    long long total) {
+    const int S = d.n_samples;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        const float v = __ldg(rf + o);
+        const float2 c = __ldg(d.carr + (int)(o % S));
+        rfc[o] = make_float2(v * c.x, v * c.y);
+    }
+}
+
+// One thread per pixel: correlate every rotated channel row with the
+// envelope at the pixel's delay, then rotate back by the pixel's phase.
+// Summation order per pixel: elements, angles, taps upwards.
+__global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const float2* __restrict__ rfc,
                                                             float* __restrict__ refl) {
-    __shared__ PulseSmem tab;
-    load_pulse_tables(d, tab);
-    __syncthreads();
     const int ix = blockIdx.x * 32 + threadIdx.x;
     const int iz = blockIdx.y * blockDim.y + threadIdx.y;
     const int f = blockIdx.z;
     if (ix >= d.nx || iz >= d.nz) return;
     const int S = d.n_samples, NE = d.n_elem, A = d.n_angles;
     const float zs = __ldg(d.zs + iz);
+    const float h = expf(-2.f * d.beta);
+    const uint64_t h2 = f2(h, h);
     float acc = 0.f;
     for (int n = 0; n < NE; ++n) {
         const float exc = rx_excess(__ldg(d.dxs + (size_t)n * d.nx + ix), zs);
@@ -758,27 +794,30 @@ __global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const floa
             int i;
             float phi;
             pixel_delay(d, a, ix, iz, exc, i, phi);
-            const float* row = rf + ((size_t)(f * A + a) * NE + n) * S;
-            const PulseAt p = pulse_at(d, phi);
-            float s = 0.f, gj = 1.f;
-            for (int j = 0; j <= p.jhi; ++j) {
-                const int m = i + j;
-                if ((unsigned)m < (unsigned)S) {
-                    float car = fmaf(tab.c[j + kJ], p.cph, tab.s[j + kJ] * p.sph);
-                    s = fmaf(__ldg(row + m), (tab.q[j + kJ] * gj) * car, s);
-                }
-                gj *= p.g;
+            // taps of the support inside the record
+            const int j0 = max((int)ceilf(phi - d.thalf), -i);
+            const int j1 = min((int)floorf(phi + d.thalf), S - 1 - i);
+            if (j0 > j1) continue;
+            const float2* row = rfc + ((size_t)(f * A + a) * NE + n) * S + i;
+            const float t = (float)j0 - phi;
+            const float w0 = expf(-d.beta * t * t), r0 = expf(-d.beta * (2.f * t + 1.f));
+            // (w, w), (r, r), (re, im) as packed pairs
+            uint64_t w = f2(w0, w0), r = f2(r0, r0), s2 = 0;
+            const uint64_t* rp = reinterpret_cast<const uint64_t*>(row);
+#pragma unroll 4
+            for (int j = j0; j <= j1; ++j) {
+                s2 = f2_fma(w, __ldg(rp + j), s2);
+                w = f2_mul(w, r);
+                r = f2_mul(r, h2);
             }
-            gj = p.ginv;
-            for (int j = -1; j >= p.jlo; --j) {
-                const int m = i + j;
-                if ((unsigned)m < (unsigned)S) {
-                    float car = fmaf(tab.c[j + kJ], p.cph, tab.s[j + kJ] * p.sph);
-                    s = fmaf(__ldg(row + m), (tab.q[j + kJ] * gj) * car, s);
-                }
-                gj *= p.ginv;
-            }
-            acc = fmaf(p.e0, s, acc);
+            const float sr = f2_lo(s2), si = f2_hi(s2);
+            // e^{-i pi wcar (i + phi)} = conj(carr[i]) e^{-i pi wcar phi}; i lies in
+            // [-kJ, S + kJ) because some tap i + j is inside the record
+            const float2 ci = __ldg(d.carr + i);
+            float sp, cp;
+            sincospif(d.wcar * phi, &sp, &cp);
+            const float zr = ci.x * cp - ci.y * sp, zi = -(ci.x * sp + ci.y * cp);
+            acc = fmaf(zr, sr, fmaf(-zi, si, acc));
         }
     }
     refl[((size_t)f * d.nz + iz) * d.nx + ix] = acc;
@@ -787,10 +826,21 @@ __global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const floa
 int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int nf,
                               cudaStream_t st) {
     const DasDev& d = P.dev;
-    dim3 block(32, 8);
-    dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, nf);
-    synth_adjoint_kernel<<<grid, block, 0, st>>>(d, rf, refl);
-    return check_launch("synth_adjoint_kernel");
+    const long long total = (long long)nf * d.n_angles * d.n_elem * d.n_samples;
+    float2* rfc = nullptr;
+    TIDAS_CUDA(cudaMallocAsync((void**)&rfc, sizeof(float2) * (size_t)total, st));
+    const long long blocks = (total + 255) / 256;
+    synth_rotate_kernel<<<(int)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, st>>>(d, rf, rfc,
+                                                                                     total);
+    int rc = check_launch("synth_rotate_kernel");
+    if (rc == TIDAS_OK) {
+        dim3 block(32, 8);
+        dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, nf);
+        synth_adjoint_kernel<<<grid, block, 0, st>>>(d, rfc, refl);
+        rc = check_launch("synth_adjoint_kernel");
+    }
+    cudaFreeAsync(rfc, st);
+    return rc;
 }
 
 // ------------------------------------------------------- PSF / kernel fit

@@ -193,24 +193,6 @@ __device__ __forceinline__ uint64_t* row_word(uint8_t* row, int c, int swz16) {
     return reinterpret_cast<uint64_t*>(row + (((c << 1) & 0x78) ^ swz16));
 }
 
-// Two single-precision FMAs / products in one packed instruction (sm_100
-// f32x2): each half is rounded exactly as the scalar fmaf / multiply.
-__device__ __forceinline__ uint64_t f2(float lo, float hi) {
-    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
-__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 // Hand-off between group g's 128 builders and its MMA warp (160 threads):
 // a barrier that both sides wait on, once per round, which also tells every
 // participant whether any of them has given up.  While the builders write

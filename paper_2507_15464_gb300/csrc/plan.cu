@@ -154,6 +154,13 @@ extern "C" int das_plan_create(const das_params* params, das_plan* out_plan) {
         ptab[(2 * kJ + 1) + j + kJ] = (float)cos(M_PI * P->wcar * j);
         ptab[2 * (2 * kJ + 1) + j + kJ] = (float)sin(M_PI * P->wcar * j);
     }
+    // carrier at integer samples, e^{i pi wcar k} for k = -kJ .. S + kJ - 1, from
+    // the FP64 phase reduced modulo 2 (so that large k lose no accuracy)
+    std::vector<float2> carr((size_t)p.n_samples + 2 * kJ);
+    for (int k = -kJ; k < p.n_samples + kJ; ++k) {
+        const double ph = fmod(P->wcar * (double)k, 2.0);
+        carr[(size_t)(k + kJ)] = make_float2((float)cos(M_PI * ph), (float)sin(M_PI * ph));
+    }
     std::vector<double> sncs(2 * A);
     for (int a = 0; a < A; ++a) {
         sncs[2 * a] = P->sn[a];
@@ -194,7 +201,7 @@ extern "C" int das_plan_create(const das_params* params, das_plan* out_plan) {
            o_bzf = o_bzi + al(4 * A * NZ), o_dxs = o_bzf + al(4 * A * NZ),
            o_zs = o_dxs + al(4 * (size_t)NE * NX), o_xs = o_zs + al(4 * NZ),
            o_ptab = o_xs + al(4 * NX), o_sncs = o_ptab + al(4 * ptab.size()),
-           total = o_sncs + al(8 * sncs.size());
+           o_carr = o_sncs + al(8 * sncs.size()), total = o_carr + al(8 * carr.size());
     void* blob = nullptr;
     cudaError_t e = cudaMalloc(&blob, total);
     if (e != cudaSuccess) {
@@ -210,7 +217,7 @@ extern "C" int das_plan_create(const das_params* params, das_plan* out_plan) {
               {o_bzi, bzi.data(), 4 * bzi.size()}, {o_bzf, bzf.data(), 4 * bzf.size()},
               {o_dxs, dxs.data(), 4 * dxs.size()}, {o_zs, zs.data(), 4 * zs.size()},
               {o_xs, xs.data(), 4 * xs.size()},  {o_ptab, ptab.data(), 4 * ptab.size()},
-              {o_sncs, sncs.data(), 8 * sncs.size()}};
+              {o_sncs, sncs.data(), 8 * sncs.size()}, {o_carr, carr.data(), 8 * carr.size()}};
     for (auto& u : up) {
         e = cudaMemcpy(b + u.off, u.src, u.n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -233,6 +240,7 @@ extern "C" int das_plan_create(const das_params* params, das_plan* out_plan) {
     d.beta = (float)P->beta_samples;
     d.wcar = (float)P->wcar;
     d.ptab = (const float*)(b + o_ptab);
+    d.carr = (const float2*)(b + o_carr) + kJ;
     P->d_sncs = (const double*)(b + o_sncs);
     d.bxi = (const int*)(b + o_bxi);
     d.bxf = (const float*)(b + o_bxf);
