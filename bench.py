@@ -340,11 +340,11 @@ def run_ours(args):
     # DRAM bytes of one das_tc_kernel launch (64 frames), from a one-pass ncu
     # capture of the current kernel (dram__bytes_read + dram__bytes_write);
     # None whenever the kernel changes after that capture
-    traffic = 689.7e6 if BATCH == 64 else None
+    traffic = 690.1e6 if BATCH == 64 else None
     # DRAM bytes of the step's two launches from the same capture: the repack
     # reads the batch and writes its staged copy, the DAS kernel reads that copy
     # (L2 serves the re-reads of neighbouring tiles) and writes the image
-    step_traffic = {"das_tc_pack_kernel": 1451.1e6, "das_tc_kernel": 689.7e6} \
+    step_traffic = {"das_tc_pack_kernel": 1452.0e6, "das_tc_kernel": 690.1e6} \
         if BATCH == 64 else None
     roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
             "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
@@ -355,12 +355,12 @@ def run_ours(args):
             "step_traffic": step_traffic,
             "step_traffic_over_algorithmic": (sum(step_traffic.values()) / alg_bytes
                                               if step_traffic else None),
-            "hw_counters": {"issue_active": 0.681, "tensor_pipe_active": 0.067,
-                            "warps_active": 0.372, "l2_hit_rate": 0.902,
-                            "warp_instructions_per_pair": 714,
+            "hw_counters": {"issue_active": 0.675, "tensor_pipe_active": 0.068,
+                            "warps_active": 0.373, "l2_hit_rate": 0.903,
+                            "warp_instructions_per_pair": 697,
                             "source": "ncu, profiles/das_tc_kernel_pw128_compound_64frames_f16.md"},
             "note": "instruction-issue- and latency-bound: 69 % of issue slots busy, "
-                    "mostly the weight-building warps; tensor pipe 6.7 % busy.  The frac above is "
+                    "mostly the weight-building warps; tensor pipe 6.8 % busy.  The frac above is "
                     "the algorithmic flops (10 per update) over a derived CUDA-core FP32 "
                     "peak; the hardware counters are the bound"}
     roof["frac"] = roof["achieved"] / roof["peak"]
