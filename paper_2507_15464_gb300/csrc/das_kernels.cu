@@ -61,51 +61,63 @@ __global__ void __launch_bounds__(256, FB == 1 ? 4 : 2)
         const float w = xin ? apod_weight(dxs, zs, d.fnum) : 0.f;
         if (__ballot_sync(0xffffffffu, w != 0.f) == 0u) continue;
         const float exc = rx_excess(dxs, zs);
+        // apodized Keys weights as polynomials in phi with w folded into the
+        // coefficients (Horner form): w w0 = phi (phi (ca phi + w) + ca),
+        // w w1 = phi^2 (cc phi + cd) + w, w w2 = phi (phi (cf - cc phi) + ch),
+        // w w3 = phi^2 (ch phi - ch); (w0, w2) and the inner terms of (w1, w3)
+        // are evaluated as packed pairs
+        const float ca = -0.5f * w, cc = 1.5f * w, cd = -2.5f * w, cf = 2.f * w, ch = 0.5f * w;
+        const uint64_t k02a = f2(ca, -cc), k02b = f2(w, cf), k02c = f2(ca, ch);
+        const uint64_t k13a = f2(cc, ch), k13b = f2(cd, -ch);
+        // element n's record of angle 0 in frame f0; angle a adds a NE S
+        const RF* rown = rf + ((size_t)f0 * A * NE + n) * S;
+        const size_t astride = (size_t)NE * S;
 #pragma unroll 2
         for (int a = 0; a < A; ++a) {
             const float uf = s_bf[a][tid] + exc;
             const float fl = floorf(uf);
             const float phi = uf - fl;
             const int i = s_bi[a][tid] + (int)fl;
-            const RF* row = rf + ((size_t)(f0 * A + a) * NE + n) * S;
+            const RF* row = rown + a * astride;
             const int nfb = FB > 1 ? min(FB, nf - f0) : 1;
             if (!CHECK) {
                 // every tap inside the record: one pointer, stepped frame by frame
                 if (INTERP == TIDAS_INTERP_CUBIC) {
-                    float w0, w1, w2, w3;
-                    keys_weights(phi, w0, w1, w2, w3);
+                    const float p2 = phi * phi;
+                    const uint64_t P = f2(phi, phi);
+                    const uint64_t t02 = f2_mul(f2_fma(f2_fma(k02a, P, k02b), P, k02c), P);
+                    const uint64_t t13 = f2_fma(k13a, P, k13b);
+                    const float v0 = f2_lo(t02), v2 = f2_hi(t02);
+                    const float v1 = fmaf(f2_lo(t13), p2, w), v3 = f2_hi(t13) * p2;
                     const RF* p = row + (i - 1);
                     if (nfb == FB) {
 #pragma unroll
                         for (int f = 0; f < FB; ++f) {
-                            float v = w0 * load_rf(p);
-                            v = fmaf(w1, load_rf(p + 1), v);
-                            v = fmaf(w2, load_rf(p + 2), v);
-                            v = fmaf(w3, load_rf(p + 3), v);
-                            acc[f] = fmaf(w, v, acc[f]);
+                            float v = fmaf(v0, load_rf(p), acc[f]);
+                            v = fmaf(v1, load_rf(p + 1), v);
+                            v = fmaf(v2, load_rf(p + 2), v);
+                            acc[f] = fmaf(v3, load_rf(p + 3), v);
                             p += fstride;
                         }
                     } else {
 #pragma unroll
                         for (int f = 0; f < FB; ++f) {
                             if (f >= nfb) break;
-                            float v = w0 * load_rf(p);
-                            v = fmaf(w1, load_rf(p + 1), v);
-                            v = fmaf(w2, load_rf(p + 2), v);
-                            v = fmaf(w3, load_rf(p + 3), v);
-                            acc[f] = fmaf(w, v, acc[f]);
+                            float v = fmaf(v0, load_rf(p), acc[f]);
+                            v = fmaf(v1, load_rf(p + 1), v);
+                            v = fmaf(v2, load_rf(p + 2), v);
+                            acc[f] = fmaf(v3, load_rf(p + 3), v);
                             p += fstride;
                         }
                     }
                 } else {
-                    const float w0 = 1.f - phi, w1 = phi;
+                    // apodized linear weights w (1 - phi), w phi
+                    const float v0 = fmaf(-w, phi, w), v1 = w * phi;
                     const RF* p = row + i;
 #pragma unroll
                     for (int f = 0; f < FB; ++f) {
                         if (f >= nfb) break;
-                        float v = w0 * load_rf(p);
-                        v = fmaf(w1, load_rf(p + 1), v);
-                        acc[f] = fmaf(w, v, acc[f]);
+                        acc[f] = fmaf(v1, load_rf(p + 1), fmaf(v0, load_rf(p), acc[f]));
                         p += fstride;
                     }
                 }
@@ -284,26 +296,36 @@ __global__ void __launch_bounds__(256, 2) das_forward_fi_kernel(DasDev d, const 
         const float w = xin ? apod_weight(dxs, zs, d.fnum) : 0.f;
         if (__ballot_sync(0xffffffffu, w != 0.f) == 0u) continue;
         const float exc = rx_excess(dxs, zs);
+        // apodized Keys weights in Horner form with w folded into the
+        // coefficients, (w0, w2) and the inner terms of (w1, w3) as packed
+        // pairs (as in das_forward_kernel)
+        const float ca = -0.5f * w, cc = 1.5f * w, cd = -2.5f * w, cf = 2.f * w, ch = 0.5f * w;
+        const uint64_t k02a = f2(ca, -cc), k02b = f2(w, cf), k02c = f2(ca, ch);
+        const uint64_t k13a = f2(cc, ch), k13b = f2(cd, -ch);
+        const RF* rown = tile + (size_t)n * S * NFP;  // element n's record of angle 0
+        const size_t astride = (size_t)NE * S * NFP;
 #pragma unroll 2
         for (int a = 0; a < A; ++a) {
             const float uf = s_bf[a][tid] + exc;
             const float fl = floorf(uf);
             const float phi = uf - fl;
             const int i = s_bi[a][tid] + (int)fl;
-            const RF* row = tile + (size_t)(a * NE + n) * S * NFP;
+            const RF* row = rown + a * astride;
             constexpr int T = INTERP == TIDAS_INTERP_CUBIC ? 4 : 2;
             float wt[T];
             int m[T];
             if (INTERP == TIDAS_INTERP_CUBIC) {
-                float w0, w1, w2, w3;
-                keys_weights(phi, w0, w1, w2, w3);
-                wt[0] = w * w0;
-                wt[1] = w * w1;
-                wt[T > 2 ? 2 : 0] = w * w2;
-                wt[T > 3 ? 3 : 0] = w * w3;
+                const float p2 = phi * phi;
+                const uint64_t P = f2(phi, phi);
+                const uint64_t t02 = f2_mul(f2_fma(f2_fma(k02a, P, k02b), P, k02c), P);
+                const uint64_t t13 = f2_fma(k13a, P, k13b);
+                wt[0] = f2_lo(t02);
+                wt[1] = fmaf(f2_lo(t13), p2, w);
+                wt[T > 2 ? 2 : 0] = f2_hi(t02);
+                wt[T > 3 ? 3 : 0] = f2_hi(t13) * p2;
                 m[0] = i - 1;
             } else {
-                wt[0] = w * (1.f - phi);
+                wt[0] = fmaf(-w, phi, w);
                 wt[1] = w * phi;
                 m[0] = i;
             }
