@@ -340,11 +340,12 @@ def run_ours(args):
     # DRAM bytes of one das_tc_kernel launch (64 frames), from a one-pass ncu
     # capture of the current kernel (dram__bytes_read + dram__bytes_write);
     # None whenever the kernel changes after that capture
-    traffic = 690.1e6 if BATCH == 64 else None
+    traffic = 688.8e6 if BATCH == 64 else None
     # DRAM bytes of the step's two launches from the same capture: the repack
-    # reads the batch and writes its staged copy, the DAS kernel reads that copy
+    # reads the plan's read window of the batch and writes its staged copy (the
+    # rest of the staging layout stays zero), the DAS kernel reads that copy
     # (L2 serves the re-reads of neighbouring tiles) and writes the image
-    step_traffic = {"das_tc_pack_kernel": 1452.0e6, "das_tc_kernel": 690.1e6} \
+    step_traffic = {"das_tc_pack_kernel": 1175.9e6, "das_tc_kernel": 688.8e6} \
         if BATCH == 64 else None
     roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp32_peak,
             "unit": "TFLOP/s", "traffic": traffic, "kernel": "das_tc_kernel",
@@ -422,10 +423,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    # A stream's first upload and last read-back overlap nothing (about 4.2 ms
-    # together); over at least 32 steps they weigh what they would in a
-    # continuing stream at most 0.13 ms per step
-    n_e2e = max(32, args.steps)
+    # A stream's first upload and last read-back overlap nothing (about 3.5 ms
+    # together); over at least 64 steps they weigh what they would in a
+    # continuing stream at most 0.06 ms per step
+    n_e2e = max(64, args.steps)
     # a plan freed by the garbage collector inside the loop would synchronise
     # the device (cudaFree) and drain the pipeline: collect first, then hold it
     import gc

@@ -76,6 +76,8 @@ struct Plan {
     // staging buffer of the repacked channel data (tensor-core DAS), grown on demand
     mutable void* tc_ws = nullptr;
     mutable size_t tc_ws_bytes = 0;
+    // layout the staging buffer was last filled in (0: unknown contents)
+    mutable long long tc_ws_layout = 0;
     mutable std::mutex tc_ws_mutex;
 };
 
@@ -151,7 +153,9 @@ namespace tidas {
 int launch_delay_table(const Plan& P, int angle, int32_t* idx, float* frac, cudaStream_t st);
 int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
 int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
-int plan_staging(const Plan& P, size_t need, void** out);
+// The plan's staging buffer, at least `need` bytes.  *fresh tells whether
+// its previous contents were written in another `layout` (or none).
+int plan_staging(const Plan& P, size_t need, void** out, long long layout, bool* fresh);
 int das_tc_prepare(Plan& P);
 int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaStream_t st);
 int launch_synthesize(const Plan& P, const double* pos, const float* amp, int n_scat, int nf,

@@ -378,7 +378,8 @@ static int das_forward_frames_inner(const Plan& P, const void* rf, float* img, i
     const int FT = (nf + NFP - 1) / NFP;
     const size_t need = (size_t)FT * R * S * NFP * sizeof(RF);
     void* ws = nullptr;
-    if (int rc = plan_staging(P, need, &ws)) return rc;
+    bool fresh = false;  // every sample of this layout is written below
+    if (int rc = plan_staging(P, need, &ws, 1, &fresh)) return rc;
     const size_t blocks = (size_t)FT * R * ((S + 63) / 64);
     if (blocks > (size_t)INT_MAX) return set_error(TIDAS_ERR_UNSUPPORTED, "das_forward: batch too large");
     frames_inner_pack_kernel<RF><<<(unsigned)blocks, 256, 0, st>>>((const RF*)rf, (RF*)ws, nf, R,

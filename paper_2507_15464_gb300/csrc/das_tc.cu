@@ -123,8 +123,10 @@ __host__ __device__ __forceinline__ int mn_swizzle(int c, int k, int NF) {
 }
 
 // [nf][R][S] FP16 -> [FT][R][Sp][NF] FP16, sample s at s + kPad, frames past
-// nf and samples outside [0, S) zero, chunks swizzled (mn_swizzle).  One
-// block per (frame tile, row, 64 samples); S is a multiple of 8.
+// nf and 8-sample chunks outside [0, S) or outside the read window
+// [rd_lo, rd_hi) zero, chunks swizzled (mn_swizzle).  One block per (frame
+// tile, row, 64-sample block sb_first .. sb_first + nbw - 1); S is a
+// multiple of 8.
 //
 // The transpose goes through shared memory as 32-bit words, each holding one
 // sample of two neighbouring frames.  Sample row r keeps its NF / 8 chunks of
@@ -133,14 +135,14 @@ __host__ __device__ __forceinline__ int mn_swizzle(int c, int k, int NF) {
 // loads that follow both touch every bank once per wavefront.
 __global__ void __launch_bounds__(256) das_tc_pack_kernel(const __half* __restrict__ rf,
                                                           __half* __restrict__ out, int nf, int R,
-                                                          int S, int Sp, int NF) {
+                                                          int S, int Sp, int NF, int sb_first,
+                                                          int nbw, int rd_lo, int rd_hi) {
     using namespace dtc;
     __shared__ uint4 tile[kPackS * 8];  // [kPackS rows][NF / 8 chunks]
     const int cpr = NF / 8;             // chunks per sample row (2, 4 or 8)
-    const int nsb = Sp / kPackS;
-    const int sb = blockIdx.x % nsb;
-    const int row = (blockIdx.x / nsb) % R;
-    const int ft = blockIdx.x / (nsb * R);
+    const int sb = sb_first + (int)(blockIdx.x % nbw);
+    const int row = (blockIdx.x / nbw) % R;
+    const int ft = blockIdx.x / (nbw * R);
     const int s0 = sb * kPackS - kPad;
     uint32_t* t32 = reinterpret_cast<uint32_t*>(tile);
     // load frame pairs x 64 samples as 16-byte chunks of 8 samples
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(256) das_tc_pack_kernel(const __half* __restri
         const int c = i % (kPackS / 8), fp = i / (kPackS / 8);
         const int s = s0 + 8 * c, fa = ft * NF + 2 * fp;
         uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-        if (s >= 0 && s < S) {
+        if (s >= 0 && s < S && s + 8 > rd_lo && s < rd_hi) {
             if (fa < nf)
                 va = __ldg(reinterpret_cast<const uint4*>(rf + ((size_t)fa * R + row) * S + s));
             if (fa + 1 < nf)
@@ -714,15 +716,18 @@ __global__ void das_tc_round_kernel(int A, int NE, int tiles, const int* __restr
 // The plan's staging buffer of das_forward (the repacked batch of either DAS
 // path), grown to `need` bytes on demand.  cudaFree / cudaMalloc synchronise
 // the device, which is why das_forward calls on one plan must not overlap.
-int plan_staging(const Plan& P, size_t need, void** out) {
+int plan_staging(const Plan& P, size_t need, void** out, long long layout, bool* fresh) {
     std::lock_guard<std::mutex> lock(P.tc_ws_mutex);
     if (need > P.tc_ws_bytes) {
+        P.tc_ws_layout = 0;
         if (P.tc_ws) TIDAS_CUDA(cudaFree(P.tc_ws));
         P.tc_ws = nullptr;
         P.tc_ws_bytes = 0;
         TIDAS_CUDA(cudaMalloc(&P.tc_ws, need));
         P.tc_ws_bytes = need;
     }
+    *fresh = P.tc_ws_layout != layout;
+    P.tc_ws_layout = layout;
     *out = P.tc_ws;
     return TIDAS_OK;
 }
@@ -785,13 +790,24 @@ int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_
     const int Sp = packed_len(d.n_samples);
     const int FT = (nf + NF - 1) / NF;
     const size_t need = (size_t)FT * R * Sp * NF * 2;
+    // Only the 64-sample blocks that meet the plan's read window (the samples
+    // any pixel weights) are packed; the rest of the staging layout is zeroed
+    // once, when the buffer comes to this layout, and stays zero.
     void* ws = nullptr;
-    if (int rc0 = plan_staging(P, need, &ws)) return rc0;
+    bool fresh = false;
+    const long long layout = 2 + NF + 256LL * FT;
+    if (int rc0 = plan_staging(P, need, &ws, layout, &fresh)) return rc0;
     __half* packed = (__half*)ws;
-    das_tc_pack_kernel<<<(unsigned)((size_t)FT * R * (Sp / kPackS)), 256, 0, st>>>(
-        (const __half*)rf, packed, nf, R, d.n_samples, Sp, NF);
-    int rc = check_launch("das_tc_pack_kernel");
-    if (rc) return rc;
+    if (fresh) TIDAS_CUDA(cudaMemsetAsync(ws, 0, need, st));
+    const int rd_lo = P.read_first, rd_hi = P.read_first + P.read_count;
+    if (rd_hi > rd_lo) {
+        const int sb_first = (rd_lo + kPad) / kPackS, sb_last = (rd_hi - 1 + kPad) / kPackS;
+        const int nbw = sb_last - sb_first + 1;
+        das_tc_pack_kernel<<<(unsigned)((size_t)FT * R * nbw), 256, 0, st>>>(
+            (const __half*)rf, packed, nf, R, d.n_samples, Sp, NF, sb_first, nbw, rd_lo, rd_hi);
+        int rc = check_launch("das_tc_pack_kernel");
+        if (rc) return rc;
+    }
     const size_t smem = smem_bytes(NF, C, A, NE);
     dim3 grid(P.tc_tiles, FT);
     if (d.interp == TIDAS_INTERP_CUBIC) {
