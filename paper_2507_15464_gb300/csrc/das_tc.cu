@@ -123,8 +123,8 @@ __host__ __device__ __forceinline__ int mn_swizzle(int c, int k, int NF) {
 }
 
 // [nf][R][S] FP16 -> [FT][R][Sp][NF] FP16, sample s at s + kPad, frames past
-// nf and 8-sample chunks outside [0, S) or outside the read window
-// [rd_lo, rd_hi) zero, chunks swizzled (mn_swizzle).  One block per (frame
+// nf and samples outside [0, S) or outside the read window [rd_lo, rd_hi)
+// zero, chunks swizzled (mn_swizzle).  One block per (frame
 // tile, row, 64-sample block sb_first .. sb_first + nbw - 1); S is a
 // multiple of 8.
 //
@@ -157,7 +157,17 @@ __global__ void __launch_bounds__(256) das_tc_pack_kernel(const __half* __restri
                 vb = __ldg(
                     reinterpret_cast<const uint4*>(rf + ((size_t)(fa + 1) * R + row) * S + s));
         }
-        const uint32_t a[4] = {va.x, va.y, va.z, va.w}, b[4] = {vb.x, vb.y, vb.z, vb.w};
+        uint32_t a[4] = {va.x, va.y, va.z, va.w}, b[4] = {vb.x, vb.y, vb.z, vb.w};
+        if (s < rd_lo || s + 8 > rd_hi) {
+            // a chunk across an end of the window: its samples outside are zero
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t keep = (s + 2 * t >= rd_lo && s + 2 * t < rd_hi ? 0x0000FFFFu : 0u) |
+                                      (s + 2 * t + 1 >= rd_lo && s + 2 * t + 1 < rd_hi ? 0xFFFF0000u : 0u);
+                a[t] &= keep;
+                b[t] &= keep;
+            }
+        }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int r0 = 8 * c + 2 * t;  // rows r0, r0 + 1 share r / 8

@@ -326,12 +326,16 @@ def test_streamer_overlapped_batches_equal_plain_forward():
         np.testing.assert_array_equal(o.numpy(), host(P.forward(b.cuda())))
 
 
-@pytest.mark.parametrize("dtype,nf,big", [("f16", 16, 6.0e4), ("f16", 3, 6.0e4), ("f32", 2, 1e30)])
+@pytest.mark.parametrize("dtype,nf,big", [("f16", 16, 6.0e4), ("f16", 3, 6.0e4), ("f32", 2, 1e30),
+                                          ("f16", 16, np.nan), ("f16", 3, np.nan),
+                                          ("f32", 2, np.nan)])
 def test_read_window_holds_every_weighted_sample(dtype, nf, big):
-    # samples outside the plan's read window, set to huge finite values,
-    # leave the image bit for bit unchanged: on the tensor cores (16 FP16
-    # frames), the frames-innermost path (3 FP16 frames) and the CUDA cores
-    # (FP32); and the windowed upload gives the same image as a full one
+    # samples outside the plan's read window, set to huge finite values or to
+    # NaN (and infinities), leave the image bit for bit unchanged: on the
+    # tensor cores (16 FP16 frames, whose repack zeroes every sample outside
+    # the window), the frames-innermost path (3 FP16 frames) and the CUDA
+    # cores (FP32), which read none of them; and the windowed upload gives
+    # the same image as a full one
     from paper_2507_15464_gb300 import capi
     g = presets.geometry("pw128_compound", nz=96, z0=20e-3)
     tdt = torch.float16 if dtype == "f16" else torch.float32
@@ -345,7 +349,7 @@ def test_read_window_holds_every_weighted_sample(dtype, nf, big):
     inside[..., first + count:] = 0.0
     outside = rf.copy()
     outside[..., :first] = big
-    outside[..., first + count:] = -big
+    outside[..., first + count:] = -big if np.isfinite(big) else np.inf
     a = host(P.forward(to_dev(inside, tdt)))
     b = host(P.forward(to_dev(outside, tdt)))
     np.testing.assert_array_equal(a, b)
