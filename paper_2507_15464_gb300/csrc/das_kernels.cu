@@ -414,17 +414,21 @@ int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaSt
 }
 
 // ------------------------------------------------------------ DAS^T
-// One block per (element, angle, frame) channel row, accumulated in shared
-// memory.  Threads walk the rows of each column (their delays are ~3 samples
-// apart, so taps of neighbouring lanes rarely collide) and add
+// One block per (element, group of ag <= kAG angles, frame): the group's channel
+// rows are accumulated in shared memory.  Threads walk the rows of each
+// column (their delays are ~3 samples apart, so taps of neighbouring lanes
+// rarely collide); the apodization and receive delay of a (pixel, element)
+// are computed once for the group's angles, and each angle adds
 // w * (interpolation weight) * img into the samples the forward pass read.
+constexpr int kAG = 4;
 template <int INTERP>
 __global__ void __launch_bounds__(256) das_adjoint_kernel(DasDev d, const float* __restrict__ img,
-                                                          float* __restrict__ rf) {
-    extern __shared__ float acc[];
-    const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
+                                                          float* __restrict__ rf, int ag) {
+    extern __shared__ float acc[];  // [ag][S]
+    const int n = blockIdx.x, a0 = blockIdx.y * ag, f = blockIdx.z;
     const int S = d.n_samples, NX = d.nx, NZ = d.nz;
-    for (int k = threadIdx.x; k < S; k += blockDim.x) acc[k] = 0.f;
+    const int na = min(ag, d.n_angles - a0);
+    for (int k = threadIdx.x; k < na * S; k += blockDim.x) acc[k] = 0.f;
     __syncthreads();
     const float* im = img + (size_t)f * NZ * NX;
     for (int ix = 0; ix < NX; ++ix) {
@@ -434,40 +438,49 @@ __global__ void __launch_bounds__(256) das_adjoint_kernel(DasDev d, const float*
             const float w = apod_weight(dxs, zs, d.fnum);
             if (w == 0.f) continue;
             const float exc = rx_excess(dxs, zs);
-            int i;
-            float phi;
-            pixel_delay(d, a, ix, iz, exc, i, phi);
             const float v = w * __ldg(im + (size_t)iz * NX + ix);
-            if (INTERP == TIDAS_INTERP_CUBIC) {
-                float w0, w1, w2, w3;
-                keys_weights(phi, w0, w1, w2, w3);
-                if ((unsigned)(i - 1) < (unsigned)S) atomicAdd(acc + i - 1, w0 * v);
-                if ((unsigned)(i) < (unsigned)S) atomicAdd(acc + i, w1 * v);
-                if ((unsigned)(i + 1) < (unsigned)S) atomicAdd(acc + i + 1, w2 * v);
-                if ((unsigned)(i + 2) < (unsigned)S) atomicAdd(acc + i + 2, w3 * v);
-            } else {
-                if ((unsigned)(i) < (unsigned)S) atomicAdd(acc + i, (1.f - phi) * v);
-                if ((unsigned)(i + 1) < (unsigned)S) atomicAdd(acc + i + 1, phi * v);
+            for (int q = 0; q < na; ++q) {
+                int i;
+                float phi;
+                pixel_delay(d, a0 + q, ix, iz, exc, i, phi);
+                float* ac = acc + q * S;
+                if (INTERP == TIDAS_INTERP_CUBIC) {
+                    float w0, w1, w2, w3;
+                    keys_weights(phi, w0, w1, w2, w3);
+                    if ((unsigned)(i - 1) < (unsigned)S) atomicAdd(ac + i - 1, w0 * v);
+                    if ((unsigned)(i) < (unsigned)S) atomicAdd(ac + i, w1 * v);
+                    if ((unsigned)(i + 1) < (unsigned)S) atomicAdd(ac + i + 1, w2 * v);
+                    if ((unsigned)(i + 2) < (unsigned)S) atomicAdd(ac + i + 2, w3 * v);
+                } else {
+                    if ((unsigned)(i) < (unsigned)S) atomicAdd(ac + i, (1.f - phi) * v);
+                    if ((unsigned)(i + 1) < (unsigned)S) atomicAdd(ac + i + 1, phi * v);
+                }
             }
         }
     }
     __syncthreads();
-    float* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
-    for (int k = threadIdx.x; k < S; k += blockDim.x) out[k] = acc[k];
+    for (int q = 0; q < na; ++q) {
+        float* out = rf + ((size_t)(f * d.n_angles + a0 + q) * d.n_elem + n) * S;
+        for (int k = threadIdx.x; k < S; k += blockDim.x) out[k] = acc[q * S + k];
+    }
 }
 
 int launch_das_adjoint(const Plan& P, const float* img, float* rf, int nf, cudaStream_t st) {
     const DasDev& d = P.dev;
-    size_t smem = (size_t)d.n_samples * sizeof(float);
-    dim3 grid(d.n_elem, d.n_angles, nf);
+    // as many angles per block as kAG rows of accumulators allow (at least one)
+    const size_t row = (size_t)d.n_samples * sizeof(float);
+    int ag = (int)min((size_t)kAG, (size_t)(200 * 1024) / row);
+    if (ag < 1) ag = 1;
+    const size_t smem = (size_t)ag * row;
+    dim3 grid(d.n_elem, (d.n_angles + ag - 1) / ag, nf);
     if (d.interp == TIDAS_INTERP_CUBIC) {
         TIDAS_CUDA(cudaFuncSetAttribute(das_adjoint_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem));
-        das_adjoint_kernel<1><<<grid, 256, smem, st>>>(d, img, rf);
+        das_adjoint_kernel<1><<<grid, 256, smem, st>>>(d, img, rf, ag);
     } else {
         TIDAS_CUDA(cudaFuncSetAttribute(das_adjoint_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem));
-        das_adjoint_kernel<0><<<grid, 256, smem, st>>>(d, img, rf);
+        das_adjoint_kernel<0><<<grid, 256, smem, st>>>(d, img, rf, ag);
     }
     return check_launch("das_adjoint_kernel");
 }
