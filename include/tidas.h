@@ -443,17 +443,19 @@ int tidas_encode(const double* samples, int32_t n, const float* lo4, const float
 
 /* Fused inference of the kernel generator (the 4-layer MLP above), no
  * hidden activations in global memory:
- *   out[i][0..63] = scale[i] * (W4 relu(W3 relu(W2 relu(W1 x_i + b1) + b2) + b3) + b4)
+ *   out[i][0..n_out-1] = scale[i] * (W4 relu(W3 relu(W2 relu(W1 x_i + b1) + b2) + b3) + b4)
  * with x_i the encoding of samples[i] (as tidas_encode; lo4 / hi4 are HOST
  * float[4] here), BF16 operands and activations, FP32 accumulation.
+ * n_out = 64 for a row kernel, kz * 64 for a band patch of kz rows: one of
+ * 64, 128, 192, 256, 512 (the last layer runs in output chunks of 256).
  *   w16  HOST array of 4 DEVICE pointers to the BF16 weights, row-major
- *        [out][in]: W1 [256][64], W2 [256][256], W3 [256][256], W4 [64][256]
- *   bias HOST array of 4 DEVICE pointers: b1, b2, b3 [256], b4 [64] float32
+ *        [out][in]: W1 [256][64], W2 [256][256], W3 [256][256], W4 [n_out][256]
+ *   bias HOST array of 4 DEVICE pointers: b1, b2, b3 [256], b4 [n_out] float32
  *   scale DEVICE float[n] or NULL (all ones); out [n][ldo] float32,
- *   ldo >= 64 and a multiple of 4, 16-byte aligned. */
+ *   ldo >= n_out and a multiple of 4, 16-byte aligned. */
 int tidas_mlp_infer(const double* samples, int64_t n, const float* lo4, const float* hi4,
                     const void* const* w16, const float* const* bias, const float* scale,
-                    float* out, int32_t ldo, void* stream);
+                    float* out, int32_t ldo, int32_t n_out, void* stream);
 
 /* Spatially varying tiDAS: Eq. (2.13) with a kernel per pixel, the kernel of
  * pixel (j, s) being the single-scatterer image of that pixel (Eq. (2.6)-

@@ -85,7 +85,7 @@ _SIG = {
                    ctypes.c_float, ctypes.c_float, _I, _P, _P, _P],
     "tidas_mse": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
     "tidas_encode": [_P, _I, _P, _P, _P, _P],
-    "tidas_mlp_infer": [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _I, _P],
+    "tidas_mlp_infer": [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _I, _I, _P],
     "tidas_fit_kernels_2d": [_P, _I, _I, _P, _P],
     "tidas_forward_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _S, _P],
     "tidas_adjoint_2d": [_P, _I, _I, _I, _I, _P, _P, _I, _I, _P, _S, _P],

@@ -252,21 +252,23 @@ class KernelMLP:
 
     # -------------------------------------------------------------- inference
     def infer(self, plan, samples, chunk=None):
-        """Kernels [n, out] (63 taps per row of SLOT) for samples [n, 4] float64
-        on the GPU.  Row kernels: one fused launch (encode, four BF16 layers,
-        scale by the apodization sum); band kernels: the layer path."""
-        if self.kz != 1:
+        """Kernels [n, out] (63 taps per row of SLOT, kz rows for a band patch)
+        for samples [n, 4] float64 on the GPU: one fused launch (encode, four
+        BF16 layers, scale by the apodization sum) for 64, 128, 192, 256 or
+        512 outputs; other band heights take the layer path."""
+        if self.out not in (64, 128, 192, 256, 512):
+            # band heights the fused kernel's output chunks do not cover
             return self.infer_layers(plan, samples)
         n = samples.shape[0]
-        out = _f32((n, OUT))
+        out = _f32((n, self.out))
         scale = _f32((n,))
         capi.call("tidas_apod_sum", plan.handle, _ptr(samples), n, _ptr(scale), _stream())
         lo = (ctypes.c_float * 4)(*BOUNDS_LO)
         hi = (ctypes.c_float * 4)(*BOUNDS_HI)
         w = (ctypes.c_void_p * 4)(*[_ptr(W) for W in self.W16])
         b = (ctypes.c_void_p * 4)(*[_ptr(v) for v in self.b])
-        capi.call("tidas_mlp_infer", _ptr(samples), n, lo, hi, w, b, _ptr(scale), _ptr(out), OUT,
-                  _stream())
+        capi.call("tidas_mlp_infer", _ptr(samples), n, lo, hi, w, b, _ptr(scale), _ptr(out),
+                  self.out, self.out, _stream())
         return out
 
     def infer_layers(self, plan, samples, chunk=131072):

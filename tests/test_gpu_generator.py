@@ -82,21 +82,26 @@ def test_apod_sum_and_encode_match_oracle():
     assert not enc[:, 4:].any()
 
 
-@pytest.mark.parametrize("n", [1, 129, 70000])
-def test_fused_inference_matches_layer_path(n):
+@pytest.mark.parametrize("n,kz", [(1, 1), (129, 1), (70000, 1), (129, 2), (300, 3), (1000, 4),
+                                  (70000, 8)])
+def test_fused_inference_matches_layer_path(n, kz):
     # tidas_mlp_infer (one launch, activations in shared memory) against the
     # layer-by-layer GEMM path on the same BF16 weights: the same products and
-    # roundings, so agreement to FP32 accumulation-order noise; ragged last tile
+    # roundings, so agreement to FP32 accumulation-order noise; ragged last
+    # tile; row kernels (64 outputs) and band patches of kz rows (kz * 64
+    # outputs, the last layer in output chunks of 256 columns)
     from paper_2507_15464_gb300.ops import DasPlan
     g = G()
     P = DasPlan(presets.geometry("pw128_compound"))
-    net = g.KernelMLP()
+    net = g.KernelMLP(kz=kz)
     u = generators.uniform((n, 4), 0.0, 1.0, (64, n), np.float64)
     lo, hi = np.array(g.BOUNDS_LO), np.array(g.BOUNDS_HI)
     s = torch.from_numpy(lo + u * (hi - lo)).cuda()
     fused = host(net.infer(P, s))
     layers = host(net.infer_layers(P, s))
-    assert rel_l2(fused[:, :63], layers[:, :63]) <= 1e-5
+    cols = 63 if kz == 1 else kz * 64
+    assert fused.shape == (n, kz * 64)
+    assert rel_l2(fused[:, :cols], layers[:, :cols]) <= 1e-5
 
 
 def test_fused_inference_matches_oracle_mlp():
