@@ -1186,7 +1186,17 @@ def bench_learned_band(torch, capi, generators, epochs, kz=8, frames=256):
     fn = lambda: ops.tidas_forward_varying(km, refl_bf, variant=capi.VARIANT_GEMM_BF16,  # noqa
                                            out=out, taps=TAPS)
     fn()
+    ms32 = time_steps(torch, fn, 5, 2, stream)
+    y32 = out.clone()
+    # the same kernels stored in BF16 once (they depend on the geometry, not on
+    # the frames): half the dominant stream, bit-identical images
+    km16 = km.to(torch.bfloat16)
+    fn = lambda: ops.tidas_forward_varying(km16, refl_bf, variant=capi.VARIANT_GEMM_BF16,  # noqa
+                                           out=out, taps=TAPS)
+    fn()
     ms = time_steps(torch, fn, 5, 2, stream)
+    same16 = bool(torch.equal(out, y32))
+    del km16, y32
     cz = kz // 2
     nu = sum(min(kz - 1, z + cz) - max(0, z + cz - (nz - 1)) + 1 for z in range(nz))
     useful = 2.0 * frames * nu * nx * TAPS
@@ -1195,9 +1205,11 @@ def bench_learned_band(torch, capi, generators, epochs, kz=8, frames=256):
                            "tensor": {"useful_tflops": useful / (ms * 1e-3) / 1e12,
                                       "peak_tflops": bf16_peak,
                                       "frac": useful / (ms * 1e-3) / 1e12 / bf16_peak},
-                           "note": "per-pixel B tiles built per (row, slice, chunk); "
-                                   "kernels read in FP32 (%.2f GB per call)"
-                                   % (nz * nx * kz * gen.SLOT * 4 / 1e9)}
+                           "fp32_kernels_ms": ms32, "bf16_kernels_image_identical": same16,
+                           "note": "per-pixel B tiles built per (row, slice, chunk); kernels "
+                                   "read in BF16 (%.2f GB per call; FP32 %.2f GB: fp32_kernels_ms)"
+                                   % (nz * nx * kz * gen.SLOT * 2 / 1e9,
+                                      nz * nx * kz * gen.SLOT * 4 / 1e9)}
 
     def nr(y):
         return float((y.double() - das).norm() / das.norm())

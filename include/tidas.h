@@ -492,6 +492,17 @@ int tidas_forward_varying_2d(const float* kernels, int32_t ld, int32_t kz, int32
 int tidas_adjoint_varying_2d(const float* kernels, int32_t ld, int32_t kz, int32_t taps,
                              int32_t nz, int32_t nx, const void* img, float* refl,
                              int32_t n_frames, int32_t variant, void* stream);
+/* The tcgen05 form of tidas_forward_varying_2d with the per-pixel kernels
+ * stored in BF16 (kernels16 [nz][nx][kz][ld] bfloat16, the same layout):
+ * half the bytes of the dominant stream.  The builders otherwise round the
+ * FP32 kernels to BF16 (round to nearest even), so kernels rounded the same
+ * way give bit-identical images.  refl bfloat16; the GEMM variant's
+ * conditions (nx % 8 == 0, 16-byte aligned arrays); kernels whose pitch ld
+ * is not a multiple of 8 are first copied to a padded stream-ordered
+ * scratch. */
+int tidas_forward_varying_2d_bf16k(const void* kernels16, int32_t ld, int32_t kz, int32_t taps,
+                                   int32_t nz, int32_t nx, const void* refl, float* img,
+                                   int32_t n_frames, void* stream);
 
 /* Per-pixel NRMSE of learned vs exact kernels (nrmse[p], may be NULL); out
  * takes the exact kernel where the NRMSE exceeds thresh, else the learned one. */

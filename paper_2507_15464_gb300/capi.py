@@ -92,6 +92,7 @@ _SIG = {
     "tidas_forward_varying": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
     "tidas_forward_varying_2d": [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P],
     "tidas_adjoint_varying_2d": [_P, _I, _I, _I, _I, _I, _P, _P, _I, _I, _P],
+    "tidas_forward_varying_2d_bf16k": [_P, _I, _I, _I, _I, _I, _P, _P, _I, _P],
     "tidas_kernel_fallback": [_P, _I, _P, _I, ctypes.c_int64, _I, ctypes.c_float, _P, _I, _P, _P],
     "tidas_row_scale": [_P, _I, _P, ctypes.c_int64, _I, _P, _I, _P],
     "tidas_band_workspace_bytes": [_I, _I, _I, _I],
@@ -209,6 +210,12 @@ def tidas_forward_varying_2d(kernels, ld, kz, taps, nz, nx, refl, img, n_frames,
                              stream=0):
     return _check(load().tidas_forward_varying_2d(kernels, ld, kz, taps, nz, nx, refl, img,
                                                   n_frames, variant, stream))
+
+
+def tidas_forward_varying_2d_bf16k(kernels16, ld, kz, taps, nz, nx, refl, img, n_frames,
+                                   stream=0):
+    return _check(load().tidas_forward_varying_2d_bf16k(kernels16, ld, kz, taps, nz, nx, refl,
+                                                        img, n_frames, stream))
 
 
 def tidas_adjoint_varying_2d(kernels, ld, kz, taps, nz, nx, img, refl, n_frames, variant,

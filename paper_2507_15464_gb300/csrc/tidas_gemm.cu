@@ -931,7 +931,7 @@ namespace vgem {
 constexpr int kStages = 3;
 constexpr int kMaxFT = 2;
 constexpr int kKOff = kMaxFT * gemm::kChunkBytes;         // kernel slice within a stage
-constexpr int kKBytes = 64 * 64 * 4;                      // 64 pixels x <= 64 FP32 taps
+constexpr int kKBytes = 64 * 64 * 4;                      // 64 pixels x <= 64 FP32 (or BF16) taps
 constexpr int kStageBytes = kKOff + kKBytes;              // 48 KB
 constexpr int kBBufs = 2;
 constexpr int kBuilders = 8;
@@ -969,6 +969,9 @@ __device__ __forceinline__ VItem vdecode(int it, int nz, int ntiles, int nm, int
 }
 }  // namespace vgem
 
+// K16: the per-pixel kernels are BF16 (half of each stage's kernel slot is
+// used); otherwise FP32, rounded to BF16 by the builders.
+template <bool K16>
 __global__ void __launch_bounds__(vgem::kThreads, 1)
     tidas_varying_gemm_kernel(const uint8_t* __restrict__ packed,
                               const __grid_constant__ CUtensorMap tmap_out,
@@ -1044,7 +1047,7 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
                             break;
                         }
                         mbar_arrive_expect_tx(&full[st],
-                                              (uint32_t)(I.nft * kChunkBytes + boxw * 64 * 4));
+                                              (uint32_t)(I.nft * kChunkBytes + boxw * 64 * (K16 ? 2 : 4)));
                         const int q = 2 * I.xt + c;
                         for (int f = 0; f < I.nft; ++f)
                             bulk_load(sA + st * vgem::kStageBytes + f * kChunkBytes,
@@ -1145,30 +1148,47 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
                               mbar_wait_or_abort(&b_empty[b], ((step >> 1) & 1) ^ 1, s_abort,
                                                  &g_wait_error, vgem::kWaitBFree);
                     if (ok) {
-                        const float* ks =
-                            reinterpret_cast<const float*>(sA + st * vgem::kStageBytes + vgem::kKOff);
-                        float v[32];
+                        const uint8_t* kslot = sA + st * vgem::kStageBytes + vgem::kKOff;
+                        // the 32 BF16 weights of this thread's four 16-byte chunks,
+                        // as pairs: word e holds inputs 2 e, 2 e + 1
+                        uint32_t wd[16];
+                        if (K16) {
+                            const uint16_t* ks = reinterpret_cast<const uint16_t*>(kslot);
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const int sl = 8 * k16_0 + e;  // pixel s0 + sl of the slice
-                            const int sx = s0 + sl;
-                            const int t = x - sx + cx;
-                            v[e] = (t >= 0 && t < taps && sx >= 0 && sx < nx) ? ks[sl * boxw + t]
-                                                                              : 0.f;
+                            for (int e = 0; e < 16; ++e) {
+                                uint32_t pr[2];
+#pragma unroll
+                                for (int k = 0; k < 2; ++k) {
+                                    const int sl = 8 * k16_0 + 2 * e + k;  // pixel s0 + sl of the slice
+                                    const int sx = s0 + sl;
+                                    const int t = x - sx + cx;
+                                    pr[k] = (t >= 0 && t < taps && sx >= 0 && sx < nx)
+                                                ? (uint32_t)ks[sl * boxw + t] : 0u;
+                                }
+                                wd[e] = pr[0] | (pr[1] << 16);
+                            }
+                        } else {
+                            const float* ks = reinterpret_cast<const float*>(kslot);
+                            float v[32];
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const int sl = 8 * k16_0 + e;  // pixel s0 + sl of the slice
+                                const int sx = s0 + sl;
+                                const int t = x - sx + cx;
+                                v[e] = (t >= 0 && t < taps && sx >= 0 && sx < nx) ? ks[sl * boxw + t]
+                                                                                  : 0.f;
+                            }
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                                wd[e] = *reinterpret_cast<const uint32_t*>(&p2);
+                            }
                         }
                         uint8_t* dst = sB + b * kBTileBytes;
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            uint32_t w4[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const __nv_bfloat162 p2 =
-                                    __floats2bfloat162_rn(v[8 * h + 2 * e], v[8 * h + 2 * e + 1]);
-                                w4[e] = *reinterpret_cast<const uint32_t*>(&p2);
-                            }
+                        for (int h = 0; h < 4; ++h)
                             *reinterpret_cast<uint4*>(dst + sw128_offset(x_rel, 8 * (k16_0 + h))) =
-                                make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                        }
+                                make_uint4(wd[4 * h], wd[4 * h + 1], wd[4 * h + 2], wd[4 * h + 3]);
                         fence_proxy_async_smem();
                     }
                     __syncwarp();
@@ -1232,19 +1252,22 @@ __global__ void __launch_bounds__(vgem::kThreads, 1)
     }
 }
 
-// rows [rows][ld] -> [rows][ldp] (the first taps columns, zero padding)
-__global__ void pad_rows_kernel(const float* __restrict__ in, int ld, int taps, long long rows,
-                                float* __restrict__ out, int ldp) {
+// rows [rows][ld] -> [rows][ldp] (the first taps columns, zero padding);
+// T is float or a 16-bit storage type
+template <typename T>
+__global__ void pad_rows_kernel(const T* __restrict__ in, int ld, int taps, long long rows,
+                                T* __restrict__ out, int ldp) {
     const long long n = rows * ldp;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
         const long long r = q / ldp;
         const int t = (int)(q - r * ldp);
-        out[q] = t < taps ? in[r * ld + t] : 0.f;
+        out[q] = t < taps ? in[r * ld + t] : T(0);
     }
 }
 
-int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int nz, int nx,
+// kern: FP32 (k16 false) or BF16 (k16 true) per-pixel kernels [nz][nx][kz][ld]
+int launch_tidas_varying_gemm(const void* kern, bool k16, int ld, int kz, int taps, int nz, int nx,
                               const void* in, float* out, int nf, cudaStream_t st) {
     CUtensorMap map_out, map_k;
     int rc = make_map_3d(&map_out, out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nz, nx, nf, 32, 32,
@@ -1257,27 +1280,34 @@ int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int n
     // kernel rows of a pitch that TMA cannot address (not a multiple of 16
     // bytes) are first copied to a padded scratch
     const long long krows = (long long)nz * nx * kz;
-    float* kpad = nullptr;
+    const int esz = k16 ? 2 : 4, per16 = 16 / esz;  // elements per 16 bytes
+    void* kpad = nullptr;
     int kld = ld;
-    if (ld % 4) {
-        kld = (taps + 3) & ~3;
-        TIDAS_CUDA(cudaMallocAsync((void**)&kpad, sizeof(float) * (size_t)krows * kld, st));
-        pad_rows_kernel<<<152 * 8, 256, 0, st>>>(kern, ld, taps, krows, kpad, kld);
+    if (ld % per16) {
+        kld = (taps + per16 - 1) / per16 * per16;
+        TIDAS_CUDA(cudaMallocAsync(&kpad, (size_t)esz * krows * kld, st));
+        if (k16)
+            pad_rows_kernel<uint16_t><<<152 * 8, 256, 0, st>>>((const uint16_t*)kern, ld, taps, krows,
+                                                               (uint16_t*)kpad, kld);
+        else
+            pad_rows_kernel<float><<<152 * 8, 256, 0, st>>>((const float*)kern, ld, taps, krows,
+                                                            (float*)kpad, kld);
         rc = check_launch("pad_rows_kernel");
         kern = kpad;
     }
     const int boxw = kld < 64 ? kld : 64;
     if (rc == TIDAS_OK) {
-        // the kernels as [pixel][slice][kld] FP32: box = boxw taps x 1 slice x 64 pixels
+        // the kernels as [pixel][slice][kld]: box = boxw taps x 1 slice x 64 pixels
         EncodeTiledFn enc = encode_fn();
         if (!enc) {
             rc = set_error(TIDAS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
         } else {
             cuuint64_t dims[3] = {(cuuint64_t)kld, (cuuint64_t)kz, (cuuint64_t)nz * nx};
-            cuuint64_t strides[2] = {(cuuint64_t)kld * 4, (cuuint64_t)kz * kld * 4};
+            cuuint64_t strides[2] = {(cuuint64_t)kld * esz, (cuuint64_t)kz * kld * esz};
             cuuint32_t box[3] = {(cuuint32_t)boxw, 1u, 64u};
             cuuint32_t estr[3] = {1u, 1u, 1u};
-            CUresult r = enc(&map_k, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(kern),
+            CUresult r = enc(&map_k, k16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                             3, const_cast<void*>(kern),
                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1303,13 +1333,13 @@ int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int n
         const int ntiles = (nx + gemm::kN - 1) / gemm::kN;
         const int items = nz * ntiles * ((nm + vgem::kMaxFT - 1) / vgem::kMaxFT);
         const int grid = items < sm_count() ? items : sm_count();
-        rc = check_cuda(cudaFuncSetAttribute(tidas_varying_gemm_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+        auto kfn = k16 ? tidas_varying_gemm_kernel<true> : tidas_varying_gemm_kernel<false>;
+        rc = check_cuda(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)vgem::kSmem),
                         "cudaFuncSetAttribute(tidas_varying_gemm_kernel)");
         if (rc == TIDAS_OK) {
-            tidas_varying_gemm_kernel<<<grid, vgem::kThreads, vgem::kSmem, st>>>(
-                packed, map_out, map_k, boxw, kz, taps, nz, nx, nf);
+            kfn<<<grid, vgem::kThreads, vgem::kSmem, st>>>(packed, map_out, map_k, boxw, kz, taps,
+                                                           nz, nx, nf);
             rc = check_launch("tidas_varying_gemm_kernel");
         }
     }

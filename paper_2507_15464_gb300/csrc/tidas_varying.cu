@@ -151,8 +151,8 @@ int varying_args(const char* who, const float* kern, int ld, int kz, int taps, i
 
 }  // namespace
 
-// tcgen05 form of the forward map (tidas_gemm.cu)
-int launch_tidas_varying_gemm(const float* kern, int ld, int kz, int taps, int nz, int nx,
+// tcgen05 form of the forward map (tidas_gemm.cu); kern FP32 or (k16) BF16
+int launch_tidas_varying_gemm(const void* kern, bool k16, int ld, int kz, int taps, int nz, int nx,
                               const void* in, float* out, int nf, cudaStream_t st);
 }  // namespace tidas
 
@@ -175,10 +175,21 @@ extern "C" int tidas_forward_varying_2d(const float* kernels, int32_t ld, int32_
                               img, n_frames, variant, true))
         return rc;
     if (variant == TIDAS_VARIANT_GEMM_BF16)
-        return launch_tidas_varying_gemm(kernels, ld, kz, taps, nz, nx, refl, img, n_frames,
+        return launch_tidas_varying_gemm(kernels, false, ld, kz, taps, nz, nx, refl, img, n_frames,
                                          (cudaStream_t)stream);
     return launch_varying_direct(false, kernels, ld, kz, taps, nz, nx, (const float*)refl, img,
                                  n_frames, (cudaStream_t)stream);
+}
+
+extern "C" int tidas_forward_varying_2d_bf16k(const void* kernels16, int32_t ld, int32_t kz,
+                                              int32_t taps, int32_t nz, int32_t nx,
+                                              const void* refl, float* img, int32_t n_frames,
+                                              void* stream) {
+    if (int rc = varying_args("tidas_forward_varying_2d_bf16k", (const float*)kernels16, ld, kz, taps,
+                              nz, nx, refl, img, n_frames, TIDAS_VARIANT_GEMM_BF16, true))
+        return rc;
+    return launch_tidas_varying_gemm(kernels16, true, ld, kz, taps, nz, nx, refl, img, n_frames,
+                                     (cudaStream_t)stream);
 }
 
 extern "C" int tidas_adjoint_varying_2d(const float* kernels, int32_t ld, int32_t kz, int32_t taps,

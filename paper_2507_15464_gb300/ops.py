@@ -280,12 +280,19 @@ def _varying(fn, kernels, x, variant, out=None, taps=None):
         nz, nx, kz, ld = kernels.shape
     taps = ld if taps is None else taps
     nf = x.shape[0]
-    _need(kernels, torch.float32, tuple(kernels.shape), "kernels")
+    k16 = kernels.dtype == torch.bfloat16
+    if k16 and (fn is not capi.tidas_forward_varying_2d or variant != capi.VARIANT_GEMM_BF16):
+        raise ValueError("BF16 kernels serve the forward tensor-core variant only")
+    _need(kernels, torch.bfloat16 if k16 else torch.float32, tuple(kernels.shape), "kernels")
     want = torch.bfloat16 if variant == capi.VARIANT_GEMM_BF16 else torch.float32
     _need(x, want, (nf, nz, nx), "input")
     out = out if out is not None else torch.empty((nf, nz, nx), dtype=torch.float32,
                                                   device=x.device)
-    fn(_ptr(kernels), ld, kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
+    if k16:
+        capi.tidas_forward_varying_2d_bf16k(_ptr(kernels), ld, kz, taps, nz, nx, _ptr(x), _ptr(out),
+                                            nf, _stream())
+    else:
+        fn(_ptr(kernels), ld, kz, taps, nz, nx, _ptr(x), _ptr(out), nf, variant, _stream())
     return out
 
 
@@ -294,8 +301,10 @@ def tidas_forward_varying(kernels, refl, variant=capi.VARIANT_DIRECT, out=None, 
     single-scatterer image): kernels [nz, nx, taps] (row form) or
     [nz, nx, kz, taps] (band form), refl [B, nz, nx] -> img [B, nz, nx].
     VARIANT_DIRECT: FP32 refl on CUDA cores; VARIANT_GEMM_BF16: BF16 refl on
-    the tcgen05 tensor cores.  The last kernel axis is the row pitch; taps
-    (default: all of it) are the columns in use."""
+    the tcgen05 tensor cores, with FP32 kernels or BF16 kernels (half the
+    bytes; FP32 kernels rounded to BF16 give the same image).  The last
+    kernel axis is the row pitch; taps (default: all of it) are the columns
+    in use."""
     return _varying(capi.tidas_forward_varying_2d, kernels, refl, variant, out, taps)
 
 

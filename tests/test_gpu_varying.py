@@ -162,3 +162,26 @@ def test_varying_gemm_full_width_band_slab():
     ref = oracle.tidas_conv_varying(k[lo:hi], xs)
     inner = slice(kz, hi - lo - kz)
     assert rel_l2(y[[0, nf - 1]][:, lo:hi][:, inner], ref[:, inner]) <= 5e-3
+
+
+@pytest.mark.parametrize("nf,nz,nx,kz,taps", GEMM_CASES)
+def test_varying_gemm_bf16_kernels_bit_identical(nf, nz, nx, kz, taps):
+    # BF16 per-pixel kernels (tidas_forward_varying_2d_bf16k): the builders
+    # otherwise round the FP32 kernels to BF16 (nearest even), so kernels
+    # rounded the same way give the same image bit for bit, at the taps' own
+    # pitch (padded copy when not a multiple of 8) and at a 64-column pitch
+    # with garbage past the taps
+    from paper_2507_15464_gb300 import capi
+    o = ops()
+    k, r = _case(nf, nz, nx, kz, taps, 78 + nx + kz)
+    x16 = to_dev(r).to(torch.bfloat16)
+    kd = to_dev(k)
+    y = host(o.tidas_forward_varying(kd, x16, variant=capi.VARIANT_GEMM_BF16))
+    y16 = host(o.tidas_forward_varying(kd.to(torch.bfloat16), x16, variant=capi.VARIANT_GEMM_BF16))
+    np.testing.assert_array_equal(y16, y)
+    kp = torch.full(tuple(k.shape[:-1]) + (64,), 3e4, dtype=torch.bfloat16, device="cuda")
+    kp[..., :taps] = kd.to(torch.bfloat16)
+    yp = host(o.tidas_forward_varying(kp, x16, variant=capi.VARIANT_GEMM_BF16, taps=taps))
+    np.testing.assert_array_equal(yp, y)
+    with pytest.raises(ValueError):
+        o.tidas_forward_varying(kd.to(torch.bfloat16), x16.float())
