@@ -155,10 +155,14 @@ int das_synthesize_adjoint(das_plan plan, const void* rf, float* refl, int32_t n
  * (Section 3.1 fixes the f-number).  Accumulation is FP32.
  *   rf  [n_frames][n_angles][n_elem][n_samples], plan's rf_dtype
  *   img [n_frames][nz][nx] float32 (output)
- * FP16 plans restage batches of two or more frames in a staging buffer the
- * plan owns (frames innermost; the tensor-core repack at >= 16 frames, see
- * DAS_OPT_TENSOR_CORES), allocated on first use and grown for larger
- * batches: das_forward calls on one FP16 plan must not overlap in time. */
+ * Every plan restages the channel data in a staging buffer the plan owns,
+ * allocated on first use and grown for larger batches: the Keys / linear
+ * polynomial coefficients of every sample interval in the read window (FP32,
+ * for up to 6 FP32 or 4 FP16 frames), frames innermost (FP16, 5 to 15
+ * frames) or the tensor-core repack (FP16, >= 16 frames, see
+ * DAS_OPT_TENSOR_CORES); FP32 batches of 7 or more frames are read in place.
+ * das_forward calls on one plan must therefore not overlap in time (issue
+ * them on one stream, or synchronise). */
 int das_forward(das_plan plan, const void* rf, float* img, int32_t n_frames, void* stream);
 
 /* Transpose of das_forward (B^T), for FP32 channel data plans:

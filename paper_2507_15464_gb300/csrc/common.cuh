@@ -153,6 +153,7 @@ namespace tidas {
 int launch_delay_table(const Plan& P, int angle, int32_t* idx, float* frac, cudaStream_t st);
 int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
 int launch_das_tc(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
+int launch_das_coeff(const Plan& P, const void* rf, float* img, int nf, cudaStream_t st);
 // The plan's staging buffer, at least `need` bytes.  *fresh tells whether
 // its previous contents were written in another `layout` (or none).
 int plan_staging(const Plan& P, size_t need, void** out, long long layout, bool* fresh);

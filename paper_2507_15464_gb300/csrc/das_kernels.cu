@@ -13,10 +13,11 @@ namespace tidas {
 // per-(pixel, element) receive correction and apodization are computed once
 // and reused for every angle; the per-(pixel, element, angle) delay and
 // interpolation weights are reused for the FB frames a thread accumulates.
-// Serves FP32 batches and single FP16 frames; FP16 batches take
-// das_forward_fi_kernel below (or the tensor cores).
+// Serves FP32 batches of seven or more frames; FP16 batches take
+// das_forward_fi_kernel below (or the tensor cores), smaller batches
+// das_coeff_kernel.
 template <typename RF, int INTERP, int FB, bool CHECK>
-__global__ void __launch_bounds__(256, FB == 1 ? 4 : 2)
+__global__ void __launch_bounds__(256, 2)
     das_forward_kernel(DasDev d, const RF* __restrict__ rf, float* __restrict__ img, int nf) {
     // per-thread transmit delay split of every angle
     __shared__ int s_bi[kMaxAngles][256];
@@ -172,15 +173,14 @@ template <typename RF, int INTERP, bool CHECK>
 static void das_forward_dispatch_fb(const DasDev& d, const void* rf, float* img, int nf,
                                     cudaStream_t st) {
     dim3 block(32, 8);
-    int fb = nf >= 16 ? 16 : (nf >= 8 ? 8 : (nf >= 4 ? 4 : (nf >= 2 ? 2 : 1)));
+    int fb = nf >= 16 ? 16 : (nf >= 8 ? 8 : (nf >= 4 ? 4 : 2));
     dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, (nf + fb - 1) / fb);
     const RF* r = (const RF*)rf;
     switch (fb) {
         case 16: das_forward_kernel<RF, INTERP, 16, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
         case 8: das_forward_kernel<RF, INTERP, 8, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
         case 4: das_forward_kernel<RF, INTERP, 4, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
-        case 2: das_forward_kernel<RF, INTERP, 2, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
-        default: das_forward_kernel<RF, INTERP, 1, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
+        default: das_forward_kernel<RF, INTERP, 2, CHECK><<<grid, block, 0, st>>>(d, r, img, nf); break;
     }
 }
 
@@ -199,8 +199,8 @@ static void das_forward_dispatch(const Plan& P, const void* rf, float* img, int 
 }
 
 // ------------------------------------------------ DAS, frames innermost
-// FP16 batches of two or more frames that do not take the tensor cores
-// (2 .. 15 frames, or the tensor cores switched off).  The batch is first
+// FP16 batches of 5 or more frames that do not take the tensor cores
+// (5 .. 15 frames, or the tensor cores switched off).  The batch is first
 // restaged as [frame tile][angle, element][sample][NFP frames] (frames past
 // nf zero), so that one tap of one pixel reads the NFP frames of its frame
 // tile as 16-byte vectors instead of NFP scalar gathers.  The delay, the
@@ -234,20 +234,15 @@ __global__ void __launch_bounds__(256) frames_inner_pack_kernel(const RF* __rest
 // the NFP frames of one (row, sample) of the restaged FP16 batch, as floats
 template <int NFP>
 __device__ __forceinline__ void load_frames(const __half* __restrict__ p, float (&v)[NFP]) {
+    static_assert(NFP % 8 == 0, "frame vectors of 16 bytes");
     uint32_t w[NFP / 2];
-    if (NFP == 4) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
-        w[0] = q.x;
-        w[1] = q.y;
-    } else {
 #pragma unroll
-        for (int j = 0; j < NFP / 8; ++j) {
-            const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + j);
-            w[4 * j] = q.x;
-            w[4 * j + 1] = q.y;
-            w[4 * j + 2] = q.z;
-            w[4 * j + 3] = q.w;
-        }
+    for (int j = 0; j < NFP / 8; ++j) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + j);
+        w[4 * j] = q.x;
+        w[4 * j + 1] = q.y;
+        w[4 * j + 2] = q.z;
+        w[4 * j + 3] = q.w;
     }
 #pragma unroll
     for (int j = 0; j < NFP / 2; ++j) {
@@ -363,7 +358,6 @@ static void das_forward_fi_dispatch(const DasDev& d, const RF* rfi, float* img, 
     dim3 block(32, 8);
     dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, (nf + NFP - 1) / NFP);
     switch (NFP) {
-        case 4: das_forward_fi_kernel<RF, INTERP, 4, CHECK><<<grid, block, 0, st>>>(d, rfi, img, nf); break;
         case 8: das_forward_fi_kernel<RF, INTERP, 8, CHECK><<<grid, block, 0, st>>>(d, rfi, img, nf); break;
         default: das_forward_fi_kernel<RF, INTERP, 16, CHECK><<<grid, block, 0, st>>>(d, rfi, img, nf); break;
     }
@@ -373,7 +367,7 @@ template <typename RF>
 static int das_forward_frames_inner(const Plan& P, const void* rf, float* img, int nf,
                                     cudaStream_t st) {
     const DasDev& d = P.dev;
-    const int NFP = nf <= 4 ? 4 : (nf <= 8 ? 8 : 16);
+    const int NFP = nf <= 8 ? 8 : 16;  // batches of 5 .. 15 frames reach here
     const int R = d.n_angles * d.n_elem, S = d.n_samples;
     const int FT = (nf + NFP - 1) / NFP;
     const size_t need = (size_t)FT * R * S * NFP * sizeof(RF);
@@ -400,16 +394,20 @@ int launch_das_forward(const Plan& P, const void* rf, float* img, int nf, cudaSt
     // batches of FP16 channel data go to the tensor cores (frames are the
     // MMA's N dimension); smaller FP16 batches are restaged with the frames
     // innermost (16-byte frame vectors per tap: 1.4x faster at 8 frames).
-    // FP32 batches and single frames read the batch in place: for FP32 the
-    // frame vectors measured no faster at 8 frames and slower at 64, where
-    // the kernel's 16 FP32 accumulators and vectors cost its occupancy.
+    // FP32 batches read the batch in place: for FP32 the frame vectors
+    // measured no faster at 8 frames and slower at 64, where the kernel's 16
+    // FP32 accumulators and vectors cost its occupancy.  Single frames and
+    // small batches read per-interval interpolation coefficients
+    // (das_coeff.cu).
     if (P.dev.rf_dtype == TIDAS_RF_F16 && P.tc_ok && P.tc_mode == 1 && nf >= 16 &&
         ((uintptr_t)rf % 16) == 0)
         return launch_das_tc(P, rf, img, nf, st);
-    if (P.dev.rf_dtype == TIDAS_RF_F16 && nf >= 2)
+    // (measured per batch size: the coefficient path up to 6 FP32 / 4 FP16
+    // frames, the sample gathers above)
+    if (nf <= (P.dev.rf_dtype == TIDAS_RF_F16 ? 4 : 6)) return launch_das_coeff(P, rf, img, nf, st);
+    if (P.dev.rf_dtype == TIDAS_RF_F16)
         return das_forward_frames_inner<__half>(P, rf, img, nf, st);
-    if (P.dev.rf_dtype == TIDAS_RF_F16) das_forward_dispatch<__half>(P, rf, img, nf, st);
-    else das_forward_dispatch<float>(P, rf, img, nf, st);
+    das_forward_dispatch<float>(P, rf, img, nf, st);
     return check_launch("das_forward_kernel");
 }
 

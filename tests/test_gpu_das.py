@@ -206,17 +206,18 @@ def test_das_ragged_grid_and_out_of_record_taps(interp):
 
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
 @pytest.mark.parametrize("interp", [0, 1])
-def test_das_frames_innermost_batches(dtype, interp):
-    # batches of 2 .. 20 frames are restaged with the frames innermost and
-    # read as frame vectors (tiles of 4, 8 or 16 frames, the last one
-    # ragged); a ragged grid whose deepest taps leave the record exercises the
-    # bounds-checked variant.  Every frame must equal the single-frame path
-    # (rounding order differs: the apodization is folded into the tap
-    # weights) and the oracle.
+def test_das_small_batches(dtype, interp):
+    # batches of 2 .. 20 frames take every CUDA-core path: per-interval
+    # coefficients with 1, 2 or 4 frames per thread (up to 6 FP32 / 4 FP16
+    # frames), FP16 frames restaged innermost and read as frame vectors
+    # (tiles of 8 or 16 frames, the last one ragged), and FP32 gathers in
+    # place; a ragged grid whose deepest taps leave the record exercises the
+    # bounds-checked variants.  Every frame must equal the single-frame path
+    # (rounding order differs between the paths) and the oracle.
     g = presets.geometry("pw64_single", nx=100, nz=77, interp=interp, n_samples=1100)
     tdt = torch.float32 if dtype == "f32" else torch.float16
     P, O = plan(g, tdt), oracle(g)
-    for nf in (2, 5, 8, 9, 13, 20):
+    for nf in (2, 3, 4, 5, 6, 8, 9, 13, 20):
         rf = generators.standard_normal((nf, 1, 64, 1100), (23, nf), np.float32)
         x = to_dev(rf, tdt)
         img = host(P.forward(x))
@@ -326,16 +327,17 @@ def test_streamer_overlapped_batches_equal_plain_forward():
         np.testing.assert_array_equal(o.numpy(), host(P.forward(b.cuda())))
 
 
-@pytest.mark.parametrize("dtype,nf,big", [("f16", 16, 6.0e4), ("f16", 3, 6.0e4), ("f32", 2, 1e30),
-                                          ("f16", 16, np.nan), ("f16", 3, np.nan),
-                                          ("f32", 2, np.nan)])
+@pytest.mark.parametrize("big", [6.0e4, np.nan])
+@pytest.mark.parametrize("dtype,nf", [("f16", 16), ("f16", 6), ("f16", 3), ("f32", 2), ("f32", 8)])
 def test_read_window_holds_every_weighted_sample(dtype, nf, big):
     # samples outside the plan's read window, set to huge finite values or to
-    # NaN (and infinities), leave the image bit for bit unchanged: on the
-    # tensor cores (16 FP16 frames, whose repack zeroes every sample outside
-    # the window), the frames-innermost path (3 FP16 frames) and the CUDA
-    # cores (FP32), which read none of them; and the windowed upload gives
-    # the same image as a full one
+    # NaN (and infinities), leave the image bit for bit unchanged on every
+    # path: the tensor cores (16 FP16 frames, whose repack zeroes every sample
+    # outside the window), the per-interval coefficients (3 FP16 and 2 FP32
+    # frames, which count samples outside the window as zero), and the
+    # frames-innermost (6 FP16 frames) and in-place (8 FP32 frames) gathers,
+    # which read none of them; and the windowed upload gives the same image as
+    # a full one
     from paper_2507_15464_gb300 import capi
     g = presets.geometry("pw128_compound", nz=96, z0=20e-3)
     tdt = torch.float16 if dtype == "f16" else torch.float32
