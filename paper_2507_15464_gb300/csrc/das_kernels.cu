@@ -648,20 +648,28 @@ __global__ void __launch_bounds__(256) synth_grid_kernel(DasDev d, const float* 
 // thread's samples k0 + q the envelope factors as
 //     env(t0 + q) = exp(-beta t0^2) R^q exp(-beta q^2),  R = exp(-2 beta t0),
 // t0 = k0 - u_p, and the last factor, the same for every pixel, is applied
-// once per sample after the sum.  No atomics; each sample is summed in a
-// fixed order (columns, then depth).
+// once per sample after the sum.  Only the nonzero pixels of each column
+// enter (compact_columns_kernel lists them in increasing depth), and
+// consecutive columns are staged together up to nz pixels per pass, so a
+// sparse map (an L1-regularised iterate) costs in proportion to its nonzeros.
+// No atomics; each sample is summed in a fixed order (columns, then depth).
 constexpr int kGS = 16;
 __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
-                                                                const float* __restrict__ reflT,
+                                                                const int* __restrict__ ccnt,
+                                                                const int* __restrict__ cz,
+                                                                const float* __restrict__ cv,
                                                                 float* __restrict__ rf) {
     extern __shared__ float sm[];
     const int NZ = d.nz, NX = d.nx, S = d.n_samples;
-    int* ui = reinterpret_cast<int*>(sm);  // [NZ] integer delay of the column's pixels
+    int* ui = reinterpret_cast<int*>(sm);  // [NZ] integer delay of the staged pixels
     float* uf = sm + NZ;                   // [NZ] fraction
     float* cre = uf + NZ;                  // [NZ] complex amplitude v e^{-i pi wcar u}
     float* cim = cre + NZ;
+    int* coff = reinterpret_cast<int*>(cim + NZ);  // [NX + 1] group column offsets
     const int n = blockIdx.x, a = blockIdx.y, f = blockIdx.z;
-    const float* rt = reflT + (size_t)f * NX * NZ;
+    const int* cnt = ccnt + (size_t)f * NX;
+    const int* czf = cz + (size_t)f * NX * NZ;
+    const float* cvf = cv + (size_t)f * NX * NZ;
     const int hi_tap = (int)ceilf(d.thalf) + 1;
     float* out = rf + ((size_t)(f * d.n_angles + a) * d.n_elem + n) * S;
     for (int base = 0; base < S; base += kGS * (int)blockDim.x) {
@@ -669,66 +677,117 @@ __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
         float gr[kGS], gi[kGS];  // G[k0 + q] / exp(-beta q^2)
 #pragma unroll
         for (int q = 0; q < kGS; ++q) gr[q] = gi[q] = 0.f;
-        for (int ix = 0; ix < NX; ++ix) {
-            __syncthreads();
-            const float dxs = __ldg(d.dxs + (size_t)n * NX + ix);
-            for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
-                int i;
-                float phi;
-                pixel_delay(d, a, ix, iz, rx_excess(dxs, __ldg(d.zs + iz)), i, phi);
-                ui[iz] = i;
-                uf[iz] = phi;
-                float v = __ldg(rt + (size_t)ix * NZ + iz);
-                // a pixel whose support misses the record adds nothing
-                if (i < -hi_tap || i >= S + hi_tap) v = 0.f;
-                float zr = 0.f, zi = 0.f;
-                if (v != 0.f) {
-                    const float2 ci = __ldg(d.carr + i);
-                    float sp, cp;
-                    sincospif(d.wcar * phi, &sp, &cp);
-                    zr = v * (ci.x * cp - ci.y * sp);
-                    zi = -v * (ci.x * sp + ci.y * cp);
-                }
-                cre[iz] = zr;
-                cim[iz] = zi;
+        for (int ix0 = 0; ix0 < NX;) {
+            // columns ix0 .. ix1 - 1 hold at most NZ nonzero pixels together
+            // (one column holds at most NZ, so a group has at least one)
+            int ix1 = ix0, tot = 0;
+            while (ix1 < NX) {
+                const int c = __ldg(cnt + ix1);
+                if (tot + c > NZ) break;
+                tot += c;
+                ++ix1;
             }
-            __syncthreads();
-            if (k0 >= S) continue;
-            // first pixel with i >= k0 - hi_tap, last with i <= k0 + kGS - 1 + hi_tap
-            int lo = 0, hi = NZ;
-            const int want_lo = k0 - hi_tap;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (ui[mid] < want_lo) lo = mid + 1; else hi = mid;
-            }
-            int lo2 = lo, hi2 = NZ;
-            const int want_hi = k0 + kGS - 1 + hi_tap;
-            while (lo2 < hi2) {
-                const int mid = (lo2 + hi2) >> 1;
-                if (ui[mid] <= want_hi) lo2 = mid + 1; else hi2 = mid;
-            }
-            for (int iz = lo; iz < lo2; ++iz) {
-                const float zr = cre[iz], zi = cim[iz];
-                if (zr == 0.f && zi == 0.f) continue;
-                const int i = ui[iz];
-                const float phi = uf[iz];
-                // this thread's samples k0 + q inside the support: tap j = k0 + q - i
-                const int j0 = k0 - i;
-                const int qlo = (int)ceilf(phi - d.thalf) - j0, qhi = (int)floorf(phi + d.thalf) - j0;
-                const float t0 = (float)j0 - phi;
-                const float e0 = expf(-d.beta * t0 * t0);
-                const float R = expf(-2.f * d.beta * t0);
-                const float er = e0 * zr, ei = e0 * zi;
-                float pw = 1.f;  // R^q
+            if (tot > 0) {
+                __syncthreads();  // the previous group has been read
+                // coff[k]: staged entries before column ix0 + k of the group
+                // (exclusive scan of the counts by the first warp)
+                const int G = ix1 - ix0;
+                if (threadIdx.x < 32) {
+                    const int lane = threadIdx.x;
+                    int run = 0;
+                    for (int k0c = 0; k0c < G; k0c += 32) {
+                        const int k = k0c + lane;
+                        const int c = k < G ? __ldg(cnt + ix0 + k) : 0;
+                        int incl = c;
 #pragma unroll
-                for (int q = 0; q < kGS; ++q) {
-                    if (q >= qlo && q <= qhi) {
-                        gr[q] = fmaf(pw, er, gr[q]);
-                        gi[q] = fmaf(pw, ei, gi[q]);
+                        for (int sh = 1; sh < 32; sh <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, incl, sh);
+                            if (lane >= sh) incl += y;
+                        }
+                        if (k < G) coff[k] = run + incl - c;
+                        run += __shfl_sync(0xffffffffu, incl, 31);
                     }
-                    pw *= R;
+                    if (lane == 0) coff[G] = run;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+                    // the group column of entry e: last k with coff[k] <= e
+                    int klo = 0, khi = G - 1;
+                    while (klo < khi) {
+                        const int mid = (klo + khi + 1) >> 1;
+                        if (coff[mid] <= e) klo = mid; else khi = mid - 1;
+                    }
+                    const int ix = ix0 + klo, j = e - coff[klo];
+                    const float dxs = __ldg(d.dxs + (size_t)n * NX + ix);
+                    {
+                        const int iz = __ldg(czf + (size_t)ix * NZ + j);
+                        float v = __ldg(cvf + (size_t)ix * NZ + j);
+                        int i;
+                        float phi;
+                        pixel_delay(d, a, ix, iz, rx_excess(dxs, __ldg(d.zs + iz)), i, phi);
+                        // a pixel whose support misses the record adds nothing
+                        if (i < -hi_tap || i >= S + hi_tap) v = 0.f;
+                        float zr = 0.f, zi = 0.f;
+                        if (v != 0.f) {
+                            const float2 ci = __ldg(d.carr + i);
+                            float sp, cp;
+                            sincospif(d.wcar * phi, &sp, &cp);
+                            zr = v * (ci.x * cp - ci.y * sp);
+                            zi = -v * (ci.x * sp + ci.y * cp);
+                        }
+                        ui[e] = i;
+                        uf[e] = phi;
+                        cre[e] = zr;
+                        cim[e] = zi;
+                    }
+                }
+                __syncthreads();
+                if (k0 < S) {
+                    int seg = 0;  // first staged entry of column ix
+                    for (int ix = ix0; ix < ix1; ++ix) {
+                        const int c = __ldg(cnt + ix);
+                        if (c == 0) continue;
+                        // first pixel with i >= k0 - hi_tap, last with i <= k0 + kGS - 1 + hi_tap
+                        int lo = seg, hi = seg + c;
+                        const int want_lo = k0 - hi_tap;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (ui[mid] < want_lo) lo = mid + 1; else hi = mid;
+                        }
+                        int lo2 = lo, hi2 = seg + c;
+                        const int want_hi = k0 + kGS - 1 + hi_tap;
+                        while (lo2 < hi2) {
+                            const int mid = (lo2 + hi2) >> 1;
+                            if (ui[mid] <= want_hi) lo2 = mid + 1; else hi2 = mid;
+                        }
+                        for (int p = lo; p < lo2; ++p) {
+                            const float zr = cre[p], zi = cim[p];
+                            if (zr == 0.f && zi == 0.f) continue;
+                            const int i = ui[p];
+                            const float phi = uf[p];
+                            // this thread's samples k0 + q inside the support: tap j = k0 + q - i
+                            const int j0 = k0 - i;
+                            const int qlo = (int)ceilf(phi - d.thalf) - j0,
+                                      qhi = (int)floorf(phi + d.thalf) - j0;
+                            const float t0 = (float)j0 - phi;
+                            const float e0 = expf(-d.beta * t0 * t0);
+                            const float R = expf(-2.f * d.beta * t0);
+                            const float er = e0 * zr, ei = e0 * zi;
+                            float pw = 1.f;  // R^q
+#pragma unroll
+                            for (int q = 0; q < kGS; ++q) {
+                                if (q >= qlo && q <= qhi) {
+                                    gr[q] = fmaf(pw, er, gr[q]);
+                                    gi[q] = fmaf(pw, ei, gi[q]);
+                                }
+                                pw *= R;
+                            }
+                        }
+                        seg += c;
+                    }
                 }
             }
+            ix0 = ix1;
         }
         if (k0 < S) {
 #pragma unroll
@@ -739,6 +798,34 @@ __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
                 }
         }
     }
+}
+
+// One warp per (frame, column) of reflT [nf][nx][nz]: the depths and values of
+// the column's nonzero pixels in increasing depth, and their count.
+__global__ void __launch_bounds__(256) compact_columns_kernel(const float* __restrict__ reflT,
+                                                              int nz, int ncols,
+                                                              int* __restrict__ cnt,
+                                                              int* __restrict__ cz,
+                                                              float* __restrict__ cv) {
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= ncols) return;  // uniform per warp
+    const float* col = reflT + (size_t)w * nz;
+    int* oz = cz + (size_t)w * nz;
+    float* ov = cv + (size_t)w * nz;
+    int c = 0;
+    for (int z0 = 0; z0 < nz; z0 += 32) {
+        const int z = z0 + lane;
+        const float v = z < nz ? col[z] : 0.f;
+        const unsigned m = __ballot_sync(0xffffffffu, v != 0.f);
+        if (v != 0.f) {
+            const int p = c + __popc(m & ((1u << lane) - 1u));
+            oz[p] = z;
+            ov[p] = v;
+        }
+        c += __popc(m);
+    }
+    if (lane == 0) cnt[w] = c;
 }
 
 // refl [nf][nz][nx] -> reflT [nf][nx][nz], 32 x 32 tiles through shared memory
@@ -762,13 +849,26 @@ __global__ void transpose_grid_kernel(const float* __restrict__ in, float* __res
 
 int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, cudaStream_t st) {
     const DasDev& d = P.dev;
-    const size_t smem_g = (size_t)4 * d.nz * sizeof(float);
+    const size_t smem_g = (size_t)4 * d.nz * sizeof(float) + (size_t)(d.nx + 1) * sizeof(int);
     if (smem_g <= 200 * 1024) {
-        float* reflT = nullptr;
-        TIDAS_CUDA(cudaMallocAsync((void**)&reflT, sizeof(float) * (size_t)nf * d.nz * d.nx, st));
+        // reflT [nf][nx][nz], then per column the count, depths and values of
+        // its nonzero pixels
+        const size_t cells = (size_t)nf * d.nz * d.nx, ncols = (size_t)nf * d.nx;
+        uint8_t* scratch = nullptr;
+        const size_t bytes = 3 * sizeof(float) * cells + sizeof(int) * ncols;
+        TIDAS_CUDA(cudaMallocAsync((void**)&scratch, bytes, st));
+        float* reflT = (float*)scratch;
+        float* cv = reflT + cells;
+        int* cz = (int*)(cv + cells);
+        int* ccnt = cz + cells;
         transpose_grid_kernel<<<dim3((d.nx + 31) / 32, (d.nz + 31) / 32, nf), dim3(32, 8), 0, st>>>(
             refl, reflT, d.nz, d.nx);
         int rc = check_launch("transpose_grid_kernel");
+        if (rc == TIDAS_OK) {
+            compact_columns_kernel<<<(unsigned)((ncols + 7) / 8), 256, 0, st>>>(reflT, d.nz, (int)ncols,
+                                                                             ccnt, cz, cv);
+            rc = check_launch("compact_columns_kernel");
+        }
         if (rc == TIDAS_OK) {
             rc = check_cuda(cudaFuncSetAttribute(synth_grid_gather_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -776,11 +876,11 @@ int launch_synthesize_grid(const Plan& P, const float* refl, float* rf, int nf, 
                             "cudaFuncSetAttribute(synth_grid_gather_kernel)");
         }
         if (rc == TIDAS_OK) {
-            synth_grid_gather_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem_g, st>>>(d, reflT,
-                                                                                        rf);
+            synth_grid_gather_kernel<<<dim3(d.n_elem, d.n_angles, nf), 256, smem_g, st>>>(
+                d, ccnt, cz, cv, rf);
             rc = check_launch("synth_grid_gather_kernel");
         }
-        cudaFreeAsync(reflT, st);
+        cudaFreeAsync(scratch, st);
         return rc;
     }
     size_t smem = (size_t)d.n_samples * sizeof(float);

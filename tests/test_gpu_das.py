@@ -279,6 +279,28 @@ def test_synthesis_grid_and_adjoint():
     dot_test(rf, y, refl, aty)
 
 
+def test_synthesis_grid_sparse_maps():
+    # the gather stages only the nonzero pixels of each column and packs
+    # consecutive columns up to nz pixels per pass: an all-zero frame, a
+    # sparse frame with empty columns, a frame whose nonzeros fill some columns
+    # completely (groups of one full column next to partial ones), and a dense
+    # frame must each match the oracle; the all-zero frame gives exact zeros
+    g = presets.geometry("pw64_single", nx=40, nz=24, z0=12e-3, n_samples=1600)
+    P, O = plan(g), oracle(g)
+    refl = np.zeros((4, 24, 40), np.float32)
+    refl[1] = generators.bernoulli_normal((24, 40), 0.03, (41,))
+    refl[1][:, 5:17] = 0.0  # empty columns
+    mixed = generators.bernoulli_normal((24, 40), 0.4, (42,))
+    mixed[:, 3] = generators.standard_normal((24,), (43,), np.float32)  # full columns
+    mixed[:, 30] = generators.standard_normal((24,), (44,), np.float32)
+    refl[2] = mixed
+    refl[3] = generators.standard_normal((24, 40), (45,), np.float32)
+    rf = host(P.synthesize_grid(to_dev(refl)))
+    assert not rf[0].any()
+    for f in (1, 2, 3):
+        assert rel_l2(rf[f], O.synth_grid(refl[f])) <= TOL32, f
+
+
 # ------------------------------------------------------------- kernel fit
 def test_fit_kernels_single_angle_all_rows():
     g = presets.geometry("pw64_single")
