@@ -911,30 +911,45 @@ __global__ void synth_rotate_kernel(DasDev d, const float* __restrict__ rf, floa
 // One thread per pixel: correlate every rotated channel row with the
 // envelope at the pixel's delay, then rotate back by the pixel's phase.
 // Summation order per pixel: elements, angles, taps upwards.
+// One thread per pixel; the transmit delay parts of every angle are staged
+// once per thread in shared memory (each thread reads only its own slots), the
+// receive correction once per (pixel, element).  The envelope values
+// exp(-beta t^2) are evaluated as 2^(-beta log2(e) t^2).
 __global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const float2* __restrict__ rfc,
                                                             float* __restrict__ refl) {
-    const int ix = blockIdx.x * 32 + threadIdx.x;
+    extern __shared__ int2 s_tx[];  // [A][256]: transmit integer part, fraction bits
+    const int lane = threadIdx.x;
+    const int tid = threadIdx.y * 32 + lane;
+    const int ix = blockIdx.x * 32 + lane;
     const int iz = blockIdx.y * blockDim.y + threadIdx.y;
     const int f = blockIdx.z;
-    if (ix >= d.nx || iz >= d.nz) return;
-    const int S = d.n_samples, NE = d.n_elem, A = d.n_angles;
+    if (ix >= d.nx || iz >= d.nz) return;  // no barrier follows
+    const int S = d.n_samples, NE = d.n_elem, A = d.n_angles, NX = d.nx;
+    for (int a = 0; a < A; ++a)
+        s_tx[a * 256 + tid] =
+            make_int2(__ldg(d.bxi + a * NX + ix) + __ldg(d.bzi + a * d.nz + iz),
+                      __float_as_int(__ldg(d.bxf + a * NX + ix) + __ldg(d.bzf + a * d.nz + iz)));
     const float zs = __ldg(d.zs + iz);
-    const float h = expf(-2.f * d.beta);
+    const float nb = -d.beta * 1.4426950408889634f;  // exp(-beta x) = 2^(nb x)
+    const float h = exp2f(2.f * nb);                  // exp(-2 beta)
     const uint64_t h2 = f2(h, h);
     float acc = 0.f;
     for (int n = 0; n < NE; ++n) {
-        const float exc = rx_excess(__ldg(d.dxs + (size_t)n * d.nx + ix), zs);
+        const float exc = rx_excess(__ldg(d.dxs + (size_t)n * NX + ix), zs);
+        const float2* rown = rfc + ((size_t)f * A * NE + n) * S;
         for (int a = 0; a < A; ++a) {
-            int i;
-            float phi;
-            pixel_delay(d, a, ix, iz, exc, i, phi);
+            const int2 b = s_tx[a * 256 + tid];
+            const float uf = __int_as_float(b.y) + exc;
+            const float fl = floorf(uf);
+            const float phi = uf - fl;
+            const int i = b.x + (int)fl;
             // taps of the support inside the record
             const int j0 = max((int)ceilf(phi - d.thalf), -i);
             const int j1 = min((int)floorf(phi + d.thalf), S - 1 - i);
             if (j0 > j1) continue;
-            const float2* row = rfc + ((size_t)(f * A + a) * NE + n) * S + i;
+            const float2* row = rown + (size_t)a * NE * S + i;
             const float t = (float)j0 - phi;
-            const float w0 = expf(-d.beta * t * t), r0 = expf(-d.beta * (2.f * t + 1.f));
+            const float w0 = exp2f(nb * t * t), r0 = exp2f(nb * (2.f * t + 1.f));
             // (w, w), (r, r), (re, im) as packed pairs
             uint64_t w = f2(w0, w0), r = f2(r0, r0), s2 = 0;
             const uint64_t* rp = reinterpret_cast<const uint64_t*>(row);
@@ -954,7 +969,7 @@ __global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const floa
             acc = fmaf(zr, sr, fmaf(-zi, si, acc));
         }
     }
-    refl[((size_t)f * d.nz + iz) * d.nx + ix] = acc;
+    refl[((size_t)f * d.nz + iz) * NX + ix] = acc;
 }
 
 int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int nf,
@@ -970,7 +985,8 @@ int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int n
     if (rc == TIDAS_OK) {
         dim3 block(32, 8);
         dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, nf);
-        synth_adjoint_kernel<<<grid, block, 0, st>>>(d, rfc, refl);
+        synth_adjoint_kernel<<<grid, block, (size_t)d.n_angles * 256 * sizeof(int2), st>>>(d, rfc,
+                                                                                       refl);
         rc = check_launch("synth_adjoint_kernel");
     }
     cudaFreeAsync(rfc, st);
