@@ -13,7 +13,7 @@ geometry.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 python bench.py --profile-case CASE [--frames F] [--dtype f16|f32] [--variant V]
-                [--kz KZ] [--kernels N] [--iters I]
+                [--kz KZ] [--kernels N] [--iters I] [--density P]
 
 --profile-case runs one kernel case a few times on seeded random inputs of
 the benchmark's shapes and prints nothing but "ok": the command that the
@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--fista-iters", type=int, default=200)
     ap.add_argument("--profile-case", default=None,
                     choices=["das", "das_adjoint", "tidas", "tidas_adjoint", "tidas2d",
-                             "tidas2d_adjoint", "varying", "line", "mlp"])
+                             "tidas2d_adjoint", "varying", "line", "mlp", "synth",
+                             "synth_adjoint"])
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--dtype", default="f16", choices=["f16", "f32"])
     ap.add_argument("--variant", type=int, default=0)
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--kz", type=int, default=16)
     ap.add_argument("--geom", default=GEOM)
     ap.add_argument("--kernels", type=int, default=524288)
+    ap.add_argument("--density", type=float, default=1.0,
+                    help="synth: fraction of nonzero pixels of the reflectivity map")
     return ap.parse_args()
 
 
@@ -108,6 +111,19 @@ def run_profile_case(a):
         else:
             x = torch.randn(P.img_shape(a.frames), device="cuda", generator=gen)
             fn = lambda: P.adjoint(x)
+    elif a.profile_case in ("synth", "synth_adjoint"):
+        # the deconvolution geometry (1024 x 1024 grid, 11 x 128 records), one
+        # frame: a Bernoulli(density) x normal map, or random channel data
+        from tidas_workloads import generators, presets
+        gd = presets.geometry("pw128_deconv")
+        P = ops.DasPlan(gd)
+        if a.profile_case == "synth":
+            x = torch.from_numpy(generators.bernoulli_normal(
+                (1, gd["nz"], gd["nx"]), a.density, (3,))).cuda()
+            fn = lambda: P.synthesize_grid(x)
+        else:
+            x = torch.randn(P.rf_shape(1), device="cuda", generator=gen)
+            fn = lambda: P.synthesize_adjoint(x)
     elif a.profile_case == "varying":
         # per-pixel kernels at the generator's layout: kz rows of 64 columns
         # (63 taps) per pixel (row form at kz = 1, band form above)
