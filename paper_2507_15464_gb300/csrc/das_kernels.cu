@@ -972,9 +972,186 @@ __global__ void __launch_bounds__(256) synth_adjoint_kernel(DasDev d, const floa
     refl[((size_t)f * d.nz + iz) * NX + ix] = acc;
 }
 
+// Moment form of the same correlation (fast Gaussian gridding, Greengard and
+// Lee 2004, with the cross term expanded in a Taylor series).  Over the taps
+// j of the core [clo, chi], which every fraction phi in [0, 1) keeps in the
+// support,
+//     sum_j rfc[i + j] env(j - phi) = e^{-beta phi^2} sum_j rfc[i + j] e^{-beta j^2} e^{a s_j},
+// s_j = j / JS, a = 2 beta JS phi, and e^{a s} = sum_m a^m s^m / m!, so
+//     = e^{-beta phi^2} sum_m (a^m / m!) N_m[i],  N_m[i] = sum_j rfc[i + j] e^{-beta j^2} s_j^m.
+// With a <= 0.8 the first omitted term (m = kMom) is below a^10 e^a / 10! < 1e-8 of
+// sum |rfc env|.  The moments are computed once per (record, sample); a pixel
+// then reads kMom / 2 float4 planes and adds the taps clo - 1 and chi + 1, which
+// belong to the support for some fractions only, directly.
+constexpr int kMom = 10;
+constexpr int kMomMaxCore = 64;
+
+// One thread per (record, sample index ip = i + P): the rotated record window
+// of the block is staged in shared memory (zero outside the record).
+__global__ void __launch_bounds__(256) synth_moments_kernel(DasDev d, const float* __restrict__ rf,
+                                                            float4* __restrict__ planes, int clo,
+                                                            int nc, int js, int pad, int li) {
+    extern __shared__ float2 smw[];              // [256 + nc - 1]
+    __shared__ float tab[kMomMaxCore * kMom];    // [nc][kMom]: e^{-beta j^2} (j / js)^m
+    const int R = d.n_angles * d.n_elem, S = d.n_samples;
+    const int row = blockIdx.y, f = blockIdx.z;
+    const int ip0 = blockIdx.x * 256;
+    const int w0 = ip0 - pad + clo;              // sample of smw[0]
+    const float* x = rf + ((size_t)f * R + row) * S;
+    const float nb = -d.beta * 1.4426950408889634f;  // exp(-beta v) = 2^(nb v)
+    for (int t = threadIdx.x; t < 256 + nc - 1; t += blockDim.x) {
+        const int m = w0 + t;
+        float2 v = make_float2(0.f, 0.f);
+        if (m >= 0 && m < S) {
+            const float r = __ldg(x + m);
+            const float2 c = __ldg(d.carr + m);
+            v = make_float2(r * c.x, r * c.y);
+        }
+        smw[t] = v;
+    }
+    for (int t = threadIdx.x; t < nc * kMom; t += blockDim.x) {
+        const int k = t / kMom, mm = t - k * kMom;
+        const int j = clo + k;
+        const float sj = (float)j / (float)js;
+        float pw = 1.f;
+        for (int q = 0; q < mm; ++q) pw *= sj;
+        tab[t] = exp2f(nb * (float)(j * j)) * pw;
+    }
+    __syncthreads();
+    const int ip = ip0 + threadIdx.x;
+    if (ip >= li) return;  // no barrier follows
+    float nr[kMom], ni[kMom];
+#pragma unroll
+    for (int mm = 0; mm < kMom; ++mm) nr[mm] = ni[mm] = 0.f;
+    for (int k = 0; k < nc; ++k) {
+        const float2 v = smw[threadIdx.x + k];
+#pragma unroll
+        for (int mm = 0; mm < kMom; ++mm) {
+            const float t = tab[k * kMom + mm];
+            nr[mm] = fmaf(v.x, t, nr[mm]);
+            ni[mm] = fmaf(v.y, t, ni[mm]);
+        }
+    }
+    float4* out = planes + ((size_t)f * R + row) * (kMom / 2) * li + ip;
+#pragma unroll
+    for (int k = 0; k < kMom / 2; ++k)
+        out[(size_t)k * li] = make_float4(nr[2 * k], ni[2 * k], nr[2 * k + 1], ni[2 * k + 1]);
+}
+
+// synth_adjoint_kernel with the core taps from the moment planes.
+__global__ void __launch_bounds__(256) synth_adjoint_mom_kernel(DasDev d, const float* __restrict__ rf,
+                                                                const float4* __restrict__ planes,
+                                                                float* __restrict__ refl, int clo,
+                                                                int chi, float ascale, int pad,
+                                                                int li) {
+    extern __shared__ int2 s_tx[];  // [A][256]: transmit integer part, fraction bits
+    const int lane = threadIdx.x;
+    const int tid = threadIdx.y * 32 + lane;
+    const int ix = blockIdx.x * 32 + lane;
+    const int iz = blockIdx.y * blockDim.y + threadIdx.y;
+    const int f = blockIdx.z;
+    if (ix >= d.nx || iz >= d.nz) return;  // no barrier follows
+    const int S = d.n_samples, NE = d.n_elem, A = d.n_angles, NX = d.nx;
+    for (int a = 0; a < A; ++a)
+        s_tx[a * 256 + tid] =
+            make_int2(__ldg(d.bxi + a * NX + ix) + __ldg(d.bzi + a * d.nz + iz),
+                      __float_as_int(__ldg(d.bxf + a * NX + ix) + __ldg(d.bzf + a * d.nz + iz)));
+    const float zs = __ldg(d.zs + iz);
+    const float nb = -d.beta * 1.4426950408889634f;  // exp(-beta x) = 2^(nb x)
+    const int jl = clo - 1, jh = chi + 1;
+    float acc = 0.f;
+    for (int n = 0; n < NE; ++n) {
+        const float exc = rx_excess(__ldg(d.dxs + (size_t)n * NX + ix), zs);
+        for (int a = 0; a < A; ++a) {
+            const int2 b = s_tx[a * 256 + tid];
+            const float uf = __int_as_float(b.y) + exc;
+            const float fl = floorf(uf);
+            const float phi = uf - fl;
+            const int i = b.x + (int)fl;
+            if (i < -pad || i >= S + pad) continue;  // no tap inside the record
+            const int row = (f * A + a) * NE + n;
+            const float4* q = planes + (size_t)row * (kMom / 2) * li + (i + pad);
+            const float4 v0 = __ldg(q), v1 = __ldg(q + li), v2 = __ldg(q + 2 * (size_t)li),
+                         v3 = __ldg(q + 3 * (size_t)li), v4 = __ldg(q + 4 * (size_t)li);
+            // sum_m (a^m / m!) N_m by Horner's rule, a = ascale phi
+            const float av = ascale * phi;
+            float pr = v4.z, pi = v4.w, c;
+            c = av * (1.f / 9.f); pr = fmaf(pr, c, v4.x); pi = fmaf(pi, c, v4.y);
+            c = av * (1.f / 8.f); pr = fmaf(pr, c, v3.z); pi = fmaf(pi, c, v3.w);
+            c = av * (1.f / 7.f); pr = fmaf(pr, c, v3.x); pi = fmaf(pi, c, v3.y);
+            c = av * (1.f / 6.f); pr = fmaf(pr, c, v2.z); pi = fmaf(pi, c, v2.w);
+            c = av * (1.f / 5.f); pr = fmaf(pr, c, v2.x); pi = fmaf(pi, c, v2.y);
+            c = av * (1.f / 4.f); pr = fmaf(pr, c, v1.z); pi = fmaf(pi, c, v1.w);
+            c = av * (1.f / 3.f); pr = fmaf(pr, c, v1.x); pi = fmaf(pi, c, v1.y);
+            c = av * 0.5f;        pr = fmaf(pr, c, v0.z); pi = fmaf(pi, c, v0.w);
+            pr = fmaf(pr, av, v0.x);
+            pi = fmaf(pi, av, v0.y);
+            const float e0 = exp2f(nb * phi * phi);
+            float sr = pr * e0, si = pi * e0;
+            // the two taps next to the core, where the support reaches them
+            const float* x = rf + (size_t)row * S;
+            if (jl >= (int)ceilf(phi - d.thalf)) {
+                const int k = i + jl;
+                if (k >= 0 && k < S) {
+                    const float t = (float)jl - phi;
+                    const float w = __ldg(x + k) * exp2f(nb * t * t);
+                    const float2 ck = __ldg(d.carr + k);
+                    sr = fmaf(w, ck.x, sr);
+                    si = fmaf(w, ck.y, si);
+                }
+            }
+            if (jh <= (int)floorf(phi + d.thalf)) {
+                const int k = i + jh;
+                if (k >= 0 && k < S) {
+                    const float t = (float)jh - phi;
+                    const float w = __ldg(x + k) * exp2f(nb * t * t);
+                    const float2 ck = __ldg(d.carr + k);
+                    sr = fmaf(w, ck.x, sr);
+                    si = fmaf(w, ck.y, si);
+                }
+            }
+            // e^{-i pi wcar (i + phi)} = conj(carr[i]) e^{-i pi wcar phi}; i lies in
+            // [-kJ, S + kJ) because some tap i + j is inside the record
+            const float2 ci = __ldg(d.carr + i);
+            float sp, cp;
+            sincospif(d.wcar * phi, &sp, &cp);
+            const float zr = ci.x * cp - ci.y * sp, zi = -(ci.x * sp + ci.y * cp);
+            acc = fmaf(zr, sr, fmaf(-zi, si, acc));
+        }
+    }
+    refl[((size_t)f * d.nz + iz) * NX + ix] = acc;
+}
+
 int launch_synthesize_adjoint(const Plan& P, const float* rf, float* refl, int nf,
                               cudaStream_t st) {
     const DasDev& d = P.dev;
+    // moment form when the core fits the table and the Taylor bound holds
+    const int clo = (int)ceilf(1.f - d.thalf), chi = (int)floorf(d.thalf);
+    const int nc = chi - clo + 1;
+    const int js = max(max(-clo, chi), 1);
+    const float ascale = 2.f * d.beta * (float)js;
+    const int pad = chi + 2;
+    const int li = d.n_samples + 2 * pad;
+    const int R = d.n_angles * d.n_elem;
+    if (nc >= 1 && nc <= kMomMaxCore && ascale <= 0.8f && clo <= 0 && chi >= 0 &&
+        (long long)nf * R <= 65535LL * 65535LL && R <= 65535 && nf <= 65535) {
+        float4* planes = nullptr;
+        const size_t bytes = (size_t)nf * R * (kMom / 2) * li * sizeof(float4);
+        TIDAS_CUDA(cudaMallocAsync((void**)&planes, bytes, st));
+        synth_moments_kernel<<<dim3((li + 255) / 256, R, nf), 256,
+                               (size_t)(256 + nc - 1) * sizeof(float2), st>>>(d, rf, planes, clo, nc,
+                                                                             js, pad, li);
+        int rc = check_launch("synth_moments_kernel");
+        if (rc == TIDAS_OK) {
+            dim3 block(32, 8);
+            dim3 grid((d.nx + 31) / 32, (d.nz + 7) / 8, nf);
+            synth_adjoint_mom_kernel<<<grid, block, (size_t)d.n_angles * 256 * sizeof(int2), st>>>(
+                d, rf, planes, refl, clo, chi, ascale, pad, li);
+            rc = check_launch("synth_adjoint_mom_kernel");
+        }
+        cudaFreeAsync(planes, st);
+        return rc;
+    }
     const long long total = (long long)nf * d.n_angles * d.n_elem * d.n_samples;
     float2* rfc = nullptr;
     TIDAS_CUDA(cudaMallocAsync((void**)&rfc, sizeof(float2) * (size_t)total, st));
