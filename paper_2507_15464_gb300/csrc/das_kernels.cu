@@ -754,16 +754,14 @@ __global__ void __launch_bounds__(256) synth_grid_gather_kernel(DasDev d,
                             const int mid = (lo + hi) >> 1;
                             if (ui[mid] < want_lo) lo = mid + 1; else hi = mid;
                         }
-                        int lo2 = lo, hi2 = seg + c;
+                        // the run ends at the first pixel with i > k0 + kGS - 1 + hi_tap
+                        // (a scan: in sparse columns the run is a pixel or two)
                         const int want_hi = k0 + kGS - 1 + hi_tap;
-                        while (lo2 < hi2) {
-                            const int mid = (lo2 + hi2) >> 1;
-                            if (ui[mid] <= want_hi) lo2 = mid + 1; else hi2 = mid;
-                        }
-                        for (int p = lo; p < lo2; ++p) {
+                        for (int p = lo; p < seg + c; ++p) {
+                            const int i = ui[p];
+                            if (i > want_hi) break;
                             const float zr = cre[p], zi = cim[p];
                             if (zr == 0.f && zi == 0.f) continue;
-                            const int i = ui[p];
                             const float phi = uf[p];
                             // this thread's samples k0 + q inside the support: tap j = k0 + q - i
                             const int j0 = k0 - i;
