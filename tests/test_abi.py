@@ -182,3 +182,30 @@ def test_debug_options_are_validated_on_the_host():
         with pytest.raises(capi.TidasError) as e:
             capi.tidas_set_debug_option(opt, val)
         assert e.value.code == capi.TIDAS_ERR_ARG
+
+
+@pytest.mark.parametrize("entry", ["fp32_kernels", "bf16_kernels"])
+def test_varying_calls_validate_arguments(entry):
+    # the spatially varying band calls check their arguments on the host before
+    # anything is enqueued; the integer "pointers" below are never dereferenced
+    def call(kern=256, ld=64, kz=8, taps=63, nz=8, nx=64, refl=512, img=1024, nf=1,
+             variant=capi.VARIANT_GEMM_BF16):
+        if entry == "bf16_kernels":
+            return capi.tidas_forward_varying_2d_bf16k(kern, ld, kz, taps, nz, nx, refl, img, nf)
+        return capi.tidas_forward_varying_2d(kern, ld, kz, taps, nz, nx, refl, img, nf, variant)
+
+    arg_errors = [dict(kern=None), dict(refl=None), dict(img=None),  # null pointers
+                  dict(taps=0), dict(ld=62),                         # taps, leading dimension
+                  dict(kz=0), dict(nz=0), dict(nx=0), dict(nf=0),    # empty shapes
+                  dict(refl=520)]                                    # not 16-byte aligned
+    for bad in arg_errors:
+        with pytest.raises(capi.TidasError) as e:
+            call(**bad)
+        assert e.value.code == capi.TIDAS_ERR_ARG, bad
+    with pytest.raises(capi.TidasError) as e:  # the GEMM needs nx % 8 == 0
+        call(nx=60)
+    assert e.value.code == capi.TIDAS_ERR_UNSUPPORTED
+    if entry == "fp32_kernels":
+        with pytest.raises(capi.TidasError) as e:  # no such variant
+            call(variant=9)
+        assert e.value.code == capi.TIDAS_ERR_UNSUPPORTED
